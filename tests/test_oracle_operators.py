@@ -1,0 +1,109 @@
+"""Pins for the oracle's crossover, mutation, tournament and init (not gpu)."""
+from collections import Counter
+from itertools import product
+
+import numpy as np
+import pytest
+
+import synth
+from _golden import graph, ints, load
+
+
+def test_appendix_e_crossover_and_mutation(oracle):
+    """App. E: majority vote of the three drawn parents gives (d); mutating
+    node 4 (neighbours {1, 2, 3, 5} = {B, B, B, G}) gives (e)."""
+    d = load("appE_operator_example.txt")
+    rp, ci = graph(d)
+    n = rp.size - 1
+    parents = np.stack([ints(d["parent1"]), ints(d["parent2"]), ints(d["parent3"])])
+    sel = np.zeros(n, np.uint8)
+    sel[int(d["mutate"]) - 1] = 1
+    for word in (0, 0x7FFFFFFF, 0xFFFFFFFF):  # no ties arise: any tie word works
+        child, q = oracle.operators_forced(rp, ci, parents, np.full(n, word), sel, np.full(n, word))
+        assert np.array_equal(child, ints(d["child"]))
+        assert np.array_equal(q, ints(d["mutated"]))
+
+
+def test_mode_pick_brute_force(oracle):
+    """Every multiset of up to 5 labels from {0..3}: the result is the
+    pick(u, t)-th smallest of the t most frequent labels (Eq. arg_max)."""
+    for k in range(1, 6):
+        for xs in product(range(4), repeat=k):
+            cnt = Counter(xs)
+            top = max(cnt.values())
+            ties = sorted(c for c, v in cnt.items() if v == top)
+            for u in (0, 0x40000000, 0x80000000, 0xC0000000, 0xFFFFFFFF):
+                j = (u * len(ties)) >> 32
+                assert oracle.mode_pick(np.array(xs), u) == ties[j]
+
+
+def test_tie_break_is_uniform(oracle):
+    xs = np.array([9, 3, 5, 7, 3, 5, 7, 9], np.int32)  # four labels tied at 2
+    rng = np.random.default_rng(0)
+    got = Counter(oracle.mode_pick(xs, int(u)) for u in rng.integers(0, 1 << 32, 4000))
+    assert set(got) == {3, 5, 7, 9}
+    chi2 = sum((v - 1000) ** 2 / 1000 for v in got.values())
+    assert chi2 < 21.1  # 3 dof, p < 1e-4
+
+
+def test_tournament_winner_distribution(oracle):
+    """Binary tournament on P sorted by (rank, crowding): the winner is sorted
+    position min(a, b), so P(position s) = (2 (N - s) - 1) / N^2."""
+    Np = 20
+    params = oracle.Params(pop_size=Np, n_parents=4, seed=123)
+    # Keys on a dominance chain: individual p has rank p' where p' = perm[p].
+    perm = np.random.default_rng(1).permutation(Np)
+    k1 = perm.astype(np.int64)
+    k2 = perm.astype(np.int64)
+    counts = np.zeros(Np)
+    xo_total = 0
+    for gen in range(1, 401):
+        par, xo, skip = oracle.select_parents(params, gen, k1, k2)
+        counts += np.bincount(perm[par.ravel()], minlength=Np)
+        xo_total += xo.sum()
+        assert np.all((skip >= 0) & (skip < 4))
+    total = counts.sum()
+    s = np.arange(Np)
+    exp = total * (2 * (Np - s) - 1) / Np ** 2
+    chi2 = ((counts - exp) ** 2 / exp).sum()
+    assert chi2 < 50.0  # 19 dof, p < 1e-4
+    frac = xo_total / (400 * Np)
+    assert abs(frac - 0.8) < 0.03  # crossover coin ~ C_P
+
+
+def test_init_population_uniform_labels(oracle):
+    n = 257
+    P = oracle.init_population(n, oracle.Params(pop_size=64, seed=5))
+    assert P.min() >= 0 and P.max() < n
+    counts = np.bincount(P.ravel(), minlength=n)
+    exp = P.size / n
+    chi2 = ((counts - exp) ** 2 / exp).sum()
+    assert chi2 < 256 + 6 * np.sqrt(2 * 256)
+    assert not np.array_equal(P[0], P[1])
+
+
+def test_offspring_labels_and_mutation_rate(oracle):
+    rp, ci, _ = synth.planted_partition(4, 40, 0.3, 0.02, seed=2)
+    n = rp.size - 1
+    params = oracle.Params(pop_size=16, seed=9, p_crossover=1.0, p_mutation=0.2)
+    st = oracle.population_init(rp, ci, params)
+    Q, qk1, qk2 = oracle.make_offspring(rp, ci, params, 1, st)
+    assert Q.min() >= 0 and Q.max() < n
+    intra, S = oracle.objectives(rp, ci, Q)
+    m = rp[-1] // 2
+    assert np.array_equal(qk1, m - intra) and np.array_equal(qk2, S)
+    # With C_P = 0 and M_P = 0 every child is a copy of one of its parents.
+    p0 = oracle.Params(pop_size=16, seed=9, p_crossover=0.0, p_mutation=0.0)
+    Q0, _, _ = oracle.make_offspring(rp, ci, p0, 1, st)
+    par, xo, skip = oracle.select_parents(p0, 1, st.k1, st.k2)
+    for i in range(16):
+        if not xo[i]:
+            assert np.array_equal(Q0[i], st.labels[par[i, skip[i]]])
+    # With M_P = 1 every node of positive degree takes a neighbour's label.
+    p1 = oracle.Params(pop_size=16, seed=9, p_crossover=0.0, p_mutation=1.0)
+    Q1, _, _ = oracle.make_offspring(rp, ci, p1, 1, st)
+    deg = np.diff(rp)
+    for i in range(4):
+        for v in range(n):
+            if deg[v]:
+                assert Q1[i, v] in set(st.labels[par[i, skip[i]]][ci[rp[v]:rp[v + 1]]].tolist())
