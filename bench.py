@@ -1,0 +1,403 @@
+#!/usr/bin/env python3
+"""Benchmark of the HP-MOCD generation engine (edge-evals/s).
+
+One step = one whole NSGA-II generation of Alg. 1 (crossover, mutation,
+evaluation of both objectives, environmental selection) for all N_p children,
+on the LFR-style graph of the paper's scalability setup (n = 40,000, average
+degree 20, maximum 50, tau1 = 2, tau2 = 1, communities 20-100, mu = 0.3),
+N_p = 100, E_S = 4, C_P = 0.8, M_P = 0.2. The metric is N_p * m edge-evals per
+generation divided by the device time of the generation.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+
+Prints one JSON line. Under torchrun each rank runs an independent replica
+(a separate detection job with its own seed): weak scaling, no collective on
+the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "edge-evals/s (N_p*|E|*G/time)"
+UNIT = "edge-evals/s"
+FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
+    ap.add_argument("--workload", default="lfr-40k")
+    ap.add_argument("--mu", type=float, default=0.3)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# Multi-process plumbing (host logic, covered by a gloo test on CPU)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def reduce_step(total_ms: float, units: float, world: int, device=None):
+    """(max time over ranks, sum of units over ranks)."""
+    if world == 1:
+        return total_ms, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# Workload and roofline bookkeeping
+# ---------------------------------------------------------------------------
+
+def build_workload(args):
+    import synth
+    spec = dict(synth.WORKLOADS[args.workload])
+    if spec["kind"] == "lfr":
+        rp, ci, _ = synth.workload(args.workload, seed=0, mu=args.mu)
+        desc = (f"{args.workload}: LFR-style n={spec['n']}, avg deg {spec['avg_deg']}, max {spec['max_deg']}, "
+                f"tau1 {spec['tau1']}, tau2 {spec['tau2']}, communities {spec['cmin']}-{spec['cmax']}, mu={args.mu}")
+    else:
+        rp, ci, _ = synth.workload(args.workload, seed=0)
+        desc = f"{args.workload}: planted partition {spec['n_comm']}x{spec['size']}"
+    return rp, ci, desc
+
+
+def algorithmic_bytes(n: int, m: int, np_: int, p_mut: float) -> dict:
+    """Bytes each kernel must move with no reuse beyond what it stages
+    explicitly (node-major rows of W int32; CSR int32)."""
+    W = (np_ + 3) & ~3
+    csr = 4 * (n + 1) + 4 * 2 * m
+    return {
+        "crossover": 16 * W * n,                                   # P half + Q in, next P + children out
+        "mutation": 8 * W * n + 4 * p_mut * np_ * 2 * m + csr,     # own row in, Q out, selected gathers, CSR
+        "evaluate": 4 * W * n + 4 * W * 2 * m + 8 * np_ * n + csr,  # own rows, neighbour rows, D_c RMW, CSR
+        "select": 0,
+    }
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+KERNEL_SOURCES = {"crossover": "k_variation.cu", "mutation": "k_variation.cu",
+                  "evaluate": "k_eval.cu", "select": "k_select.cu"}
+
+
+def source_digest(kernel: str) -> str:
+    path = os.path.join(ROOT, "paper_2506_01752_gb300", "csrc", KERNEL_SOURCES[kernel])
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current source of that kernel."""
+    pat = re.compile(rf"traffic_bytes_per_launch\[{kernel}@{re.escape(workload)}\]:\s*([0-9.eE+]+)\s+"
+                     r"source_sha256_16:\s*([0-9a-f]+)")
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as f:
+            for line in f:
+                mt = pat.search(line)
+                if mt and mt.group(2) == source_digest(kernel):
+                    return float(mt.group(1))
+    return None
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50",
+                 "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle legs
+# ---------------------------------------------------------------------------
+
+def cpu_oracle_sample(rp, ci, seed: int, budget_s: float = 12.0, max_gens: int = 6):
+    """The oracle as it stands, single-threaded, for whole generations of the
+    same workload until the budget is spent."""
+    import oracle
+    oracle.build()
+    params = oracle.Params(seed=seed)
+    st = oracle.population_init(rp, ci, params)
+    m = int(rp[-1] // 2)
+    gens, t0 = 0, time.perf_counter()
+    while gens < max_gens:
+        st = oracle.run(rp, ci, params, st, 1)
+        gens += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": params.pop_size * m * gens / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{gens} whole generations (N_p={params.pop_size}) of the same workload, "
+                      f"single-threaded C oracle, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    rp, ci, desc = build_workload(args)
+    oracle.build()
+    params = oracle.Params(seed=args.seed)
+    st = oracle.population_init(rp, ci, params)
+    m = int(rp[-1] // 2)
+    chunk = 10  # children per step: a bounded sample of one generation
+    gen = 1
+
+    def step(k):
+        i0 = (k * chunk) % params.pop_size
+        oracle.make_offspring_range(rp, ci, params, gen, st, i0, i0 + chunk)
+
+    for k in range(args.warmup):
+        step(k)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step(k)
+    dt = time.perf_counter() - t0
+    value = chunk * m * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": desc, "n": int(rp.size - 1), "m": m, "pop_size": params.pop_size,
+                   "step": f"{chunk} of the {params.pop_size} children of one generation "
+                           "(crossover, mutation, evaluation) by the CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} steps x {chunk} children, single-threaded C oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_mine(args):
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_2506_01752_gb300 as mocd
+    mocd.build.build()
+    rp, ci, desc = build_workload(args)
+    n = int(rp.size - 1)
+    m = int(rp[-1] // 2)
+    params = mocd.Params(seed=args.seed + rank)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = mocd.graph_upload(rp, ci, stream)
+    mocd.population_init(ctx, params)
+    mocd.set_timing(ctx, True)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+
+    index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) if world == 1 else local
+    sampler = ClockSampler(index)
+    sampler.start()
+    # Warm-up: W generations, then a short pre-roll so that clocks settle.
+    for _ in range(args.warmup):
+        mocd.generation(ctx, 1)
+    t_end = time.perf_counter() + 0.5
+    pre = 0
+    while time.perf_counter() < t_end:
+        mocd.generation(ctx, 20)
+        mocd.synchronize(ctx)
+        pre += 20
+    mocd.synchronize(ctx)
+    barrier(world)
+    torch.cuda.synchronize()
+
+    step_ms = []
+    stages = {s: [] for s in mocd.STAGES}
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()  # L2 flush between timed steps, outside the events
+        ev0.record(stream)
+        mocd.generation(ctx, 1)
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        for s, v in mocd.kernel_times(ctx).items():
+            stages[s].append(v)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+
+    total_ms, units = reduce_step(sum(step_ms), float(params.pop_size * m * args.steps), world,
+                                  device=dev if world > 1 else None)
+    value = units / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+
+    mean_stage = {s: statistics.fmean(v) for s, v in stages.items()}
+    kernels = {k: mean_stage[k] for k in ("crossover", "mutation", "evaluate", "select")}
+    dominant = max(kernels, key=kernels.get)
+    alg = algorithmic_bytes(n, m, params.pop_size, params.p_mutation)
+    peak, peak_kind = measured_peaks()
+    achieved = alg[dominant] / (kernels[dominant] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": recorded_traffic(dominant, args.workload),
+                "algorithmic_bytes_per_launch": alg[dominant],
+                "stage_ms": {k: round(v, 5) for k, v in mean_stage.items()}}
+
+    e2e = None
+    if not args.no_e2e:
+        # The same metric through the public C ABI from host buffers: upload
+        # the CSR, initialise, run `steps` generations, read the front back.
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = mocd.graph_upload(rp, ci, stream)
+        mocd.population_init(h, params)
+        mocd.generation(h, args.steps)
+        fr = mocd.pareto_front(h)
+        t1 = time.perf_counter()
+        mocd.destroy(h)
+        h2d = rp.nbytes + ci.nbytes
+        d2h = fr.labels.nbytes + fr.f1.nbytes + fr.f2.nbytes + fr.intra.nbytes + fr.sumsq.nbytes
+        e2e_t, e2e_units = reduce_step((t1 - t0) * 1e3, float(params.pop_size * m * args.steps), world,
+                                       device=dev if world > 1 else None)
+        e2e = {"value": e2e_units / (e2e_t / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "job": f"graph upload + init + {args.steps} generations + front download, host buffers"}
+
+    mocd.destroy(ctx)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(rp, ci, args.seed)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": desc, "n": n, "m": m, "pop_size": params.pop_size, "n_parents": params.n_parents,
+                       "p_crossover": params.p_crossover, "p_mutation": params.p_mutation,
+                       "step": "one generation of Alg. 1 (crossover, mutation, evaluation, selection)",
+                       "l2": f"flushed between timed steps ({FLUSH_BYTES >> 20} MB write, outside the events)",
+                       "parallelism": f"{world} independent replica(s)",
+                       "warmup_generations": args.warmup + pre},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 4 * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_mine(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

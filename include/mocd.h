@@ -1,0 +1,174 @@
+/*
+ * mocd.h -- C ABI of the GB300 (sm_103a) HP-MOCD generation engine.
+ *
+ * HP-MOCD (arXiv 2506.01752) evolves a population of N_p partitions of an
+ * undirected, unweighted graph G = (V, E) with NSGA-II (Alg. 1), minimising
+ *   f1(C) = 1 - sum_c |E(c)| / m   and   f2(C) = sum_c (sum_{v in c} deg v / 2m)^2
+ * (Eq. objectives, Sec. 4.1). One generation (Alg. 1, loop body) is:
+ * rank and crowding of P, tournament selection of E_S parents per child,
+ * topology-aware crossover (Sec. 4.3.1, Alg. 2), topology-aware mutation
+ * (Sec. 4.3.2), evaluation of both objectives for every child, and
+ * environmental selection of the next P from P u Q.
+ *
+ * Conventions for every call:
+ *   - Return value: MOCD_OK (0) or a negative MOCD_ERR_* status; a call that
+ *     fails leaves the context usable unless it returns MOCD_ERR_CUDA.
+ *   - Host pointers are read or written only during the call and stay owned
+ *     by the caller. The context owns all device memory it allocates.
+ *   - Work is issued on the context's CUDA stream; calls that return host data
+ *     synchronise that stream first. Calls on one context are not re-entrant;
+ *     separate contexts are independent.
+ *   - Labels are int32 community ids in [0, n); a label vector of an
+ *     individual is n consecutive int32 (individual-major on the host).
+ *   - Integer objective keys: k1 = m - intra, where intra = sum_c |E(c)|, and
+ *     k2 = S = sum_c D_c^2 with D_c = sum_{v in c} deg v. Then f1 = k1 / m and
+ *     f2 = S / (4 m^2), each computed as one IEEE double division. Dominance
+ *     (Sec. 2.2) compares (k1, k2) exactly.
+ *
+ * Limits: 1 <= N_p <= 128, 1 <= E_S <= 16, n < 2^30, 2m < 2^31.
+ */
+#ifndef MOCD_H
+#define MOCD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    MOCD_OK = 0,
+    MOCD_ERR_INVALID_ARG = -1,     /* null pointer, bad size or parameter, label out of range */
+    MOCD_ERR_NOT_SYMMETRIC = -2,   /* edge (u, v) present without (v, u) */
+    MOCD_ERR_SELF_LOOP = -3,       /* edge (v, v): Sec. 2.1 requires u != v */
+    MOCD_ERR_DUPLICATE_EDGE = -4,  /* repeated neighbour: E is a set */
+    MOCD_ERR_EMPTY_GRAPH = -5,     /* m = 0: f1 and f2 are undefined */
+    MOCD_ERR_OUT_OF_MEMORY = -6,   /* device allocation failed */
+    MOCD_ERR_BUFFER_TOO_SMALL = -7,/* caller's capacity below the result size (count set) */
+    MOCD_ERR_CUDA = -8,            /* a CUDA call failed */
+    MOCD_ERR_NOT_READY = -9        /* population not initialised yet */
+};
+
+typedef struct mocd_ctx mocd_ctx;  /* opaque; owns device memory and a stream */
+
+/* Alg. 1 parameters (Table of parameter settings: N_p = 100, C_P = 0.8,
+ * M_P = 0.2, E_S = 4). */
+typedef struct {
+    int32_t pop_size;     /* N_p, 1..128 */
+    int32_t n_parents;    /* E_S, parents per crossover, 1..16 */
+    double p_crossover;   /* C_P in [0, 1]: crossover iff u <= floor(C_P 2^32) */
+    double p_mutation;    /* M_P in [0, 1]: node mutates iff u < floor(M_P 2^32) */
+    uint64_t seed;        /* Philox4x32-10 key */
+    int32_t init_mode;    /* 0: labels uniform in [0, n) (Alg. 1 InitializePopulation) */
+} mocd_params;
+
+/*
+ * Upload a graph (Alg. 1 phase 1: graph storage and PrecomputeDegrees;
+ * Sec. 4.2 graph representation).
+ *   out      receives a new context (set to NULL on failure)
+ *   n        number of nodes, 1 <= n < 2^30
+ *   row_ptr  host int64[n + 1], non-decreasing, row_ptr[0] = 0
+ *   col_idx  host int32[row_ptr[n]]: symmetric adjacency (each undirected
+ *            edge in both rows), no self loops, no repeated neighbours
+ *   cuda_stream  cudaStream_t to issue work on, or NULL for a stream the
+ *            context creates and owns
+ * Errors: INVALID_ARG, NOT_SYMMETRIC, SELF_LOOP, DUPLICATE_EDGE, EMPTY_GRAPH,
+ * OUT_OF_MEMORY, CUDA.
+ */
+int mocd_graph_upload(mocd_ctx **out, int64_t n, const int64_t *row_ptr,
+                      const int32_t *col_idx, void *cuda_stream);
+
+/*
+ * Create and evaluate the initial population P^(0) (Alg. 1 phases 1-2:
+ * InitializePopulation, then EvaluateIndividual for each member), rank it and
+ * draw the tournament of generation 1. Resets the generation counter to 0.
+ * Errors: INVALID_ARG (params out of the limits above), OUT_OF_MEMORY, CUDA.
+ */
+int mocd_population_init(mocd_ctx *ctx, const mocd_params *params);
+
+/*
+ * Run n_generations generations of Alg. 1 (the "for gen" loop body), issued
+ * asynchronously on the context stream as one CUDA graph launch each.
+ * Errors: INVALID_ARG (n_generations < 0), NOT_READY, CUDA.
+ */
+int mocd_generation(mocd_ctx *ctx, int32_t n_generations);
+
+/*
+ * Pareto front of the current population (Alg. 1 phase 4):
+ * F_1 = {p in P : rank(p) = 1}, members in P order, and the recommended
+ * solution of SelectSolution (Alg. 3, Q = 1 - f1 - f2, Eq. selection; the
+ * first member with the largest Q wins).
+ *   cap      capacity (members) of the output arrays
+ *   count    receives |F_1|; if |F_1| > cap, MOCD_ERR_BUFFER_TOO_SMALL is
+ *            returned with count set and nothing else written
+ *   labels   host int32[cap * n] or NULL: labels of member k at [k * n]
+ *   f1, f2   host double[cap] or NULL
+ *   intra, sumsq  host int64[cap] or NULL: exact intra = sum_c |E(c)| and S
+ *   best     host int32 or NULL: index into the front of the recommended one
+ */
+int mocd_pareto_front(mocd_ctx *ctx, int32_t cap, int32_t *count, int32_t *labels,
+                      double *f1, double *f2, int64_t *intra, int64_t *sumsq,
+                      int32_t *best);
+
+/*
+ * Copy out the whole current population P in P order (checkpoint; also the
+ * state that environmental selection of Alg. 1 produced).
+ *   labels   host int32[N_p * n] or NULL;  k1, k2 host int64[N_p] or NULL
+ *   generation  host int32 or NULL: generations run since initialisation
+ */
+int mocd_get_population(mocd_ctx *ctx, int32_t *labels, int64_t *k1, int64_t *k2,
+                        int32_t *generation);
+
+/*
+ * Replace the population with caller labels (resume from a checkpoint): the
+ * labels are evaluated on the device (Eq. objectives), ranked, and the
+ * tournament of generation `generation + 1` is drawn, so a run resumed from
+ * mocd_get_population continues exactly as the uninterrupted run would.
+ *   params   as in mocd_population_init
+ *   labels   host int32[N_p * n], values in [0, n)
+ *   generation  number of generations already run, >= 0
+ * Errors: INVALID_ARG (labels out of range), OUT_OF_MEMORY, CUDA.
+ */
+int mocd_set_population(mocd_ctx *ctx, const mocd_params *params, const int32_t *labels,
+                        int32_t generation);
+
+/*
+ * Evaluate arbitrary labellings (Eq. objectives; Alg. 1 EvaluateIndividual):
+ *   count    number of labellings, >= 0
+ *   labels   host int32[count * n], values in [0, n)
+ *   intra, sumsq  host int64[count]: exact intra and S of each labelling
+ * Uses context-owned scratch; does not touch the population.
+ * Errors: INVALID_ARG (labels out of range), OUT_OF_MEMORY, CUDA.
+ */
+int mocd_evaluate(mocd_ctx *ctx, int32_t count, const int32_t *labels, int64_t *intra,
+                  int64_t *sumsq);
+
+/* Block until all work issued on the context stream is done. */
+int mocd_synchronize(mocd_ctx *ctx);
+
+/*
+ * Per-kernel timing of the generation step (measurement support, not part
+ * of the method): when enabled, the generation graph records CUDA events
+ * between its kernels. mocd_kernel_times writes, for the most recent
+ * generation, the duration in milliseconds of each stage, in this order:
+ * crossover, mutation, histogram clear, evaluation, selection; returns the
+ * number of stages (5) or a negative status. NOT_READY if timing is off or no
+ * generation ran since it was enabled.
+ */
+int mocd_set_timing(mocd_ctx *ctx, int32_t enable);
+int mocd_kernel_times(mocd_ctx *ctx, float *ms, int32_t cap);
+
+/* Graph size and population shape: any pointer may be NULL. */
+int mocd_info(mocd_ctx *ctx, int64_t *n, int64_t *m, int32_t *pop_size, int32_t *generation);
+
+/* Release the context and all device memory it owns. NULL is ignored. */
+void mocd_destroy(mocd_ctx *ctx);
+
+/* Static description of a status code. */
+const char *mocd_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MOCD_H */

@@ -62,6 +62,7 @@ def _load():
             "orc_init_population": (ctypes.c_int, [i64, P, P]),
             "orc_select_parents": (ctypes.c_int, [P, u32, P, P, P, P, P]),
             "orc_make_offspring": (ctypes.c_int, [i64, P, P, P, u32, P, P, P, P, P, P]),
+            "orc_make_offspring_range": (ctypes.c_int, [i64, P, P, P, u32, P, P, P, i32, i32, P, P, P]),
             "orc_env_select": (ctypes.c_int, [i32, P, P, P]),
             "orc_run": (ctypes.c_int, [i64, P, P, P, u32, i32, P, P, P]),
             "orc_population_init": (ctypes.c_int, [i64, P, P, P, P, P, P]),
@@ -246,6 +247,24 @@ def make_offspring(row_ptr, col_idx, params: Params, gen: int, state: State):
     pr = params._c()
     _check(_load().orc_make_offspring(n, _p(rp), _p(ci), ctypes.byref(pr), gen, _p(P), _p(k1), _p(k2),
                                       _p(Q), _p(qk1), _p(qk2)), "make_offspring")
+    return Q, qk1, qk2
+
+
+def make_offspring_range(row_ptr, col_idx, params: Params, gen: int, state: State, i0: int, i1: int):
+    """Children i0 <= i < i1 of generation ``gen`` (a bounded sample of one
+    generation); rows outside the range are left zero."""
+    rp, ci = _graph(row_ptr, col_idx)
+    n = rp.size - 1
+    Np = params.pop_size
+    P = np.ascontiguousarray(state.labels, dtype=np.int32)
+    k1 = np.ascontiguousarray(state.k1, dtype=np.int64)
+    k2 = np.ascontiguousarray(state.k2, dtype=np.int64)
+    Q = np.zeros((Np, n), dtype=np.int32)
+    qk1 = np.zeros(Np, dtype=np.int64)
+    qk2 = np.zeros(Np, dtype=np.int64)
+    pr = params._c()
+    _check(_load().orc_make_offspring_range(n, _p(rp), _p(ci), ctypes.byref(pr), gen, _p(P), _p(k1), _p(k2),
+                                            i0, i1, _p(Q), _p(qk1), _p(qk2)), "make_offspring_range")
     return Q, qk1, qk2
 
 

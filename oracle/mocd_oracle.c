@@ -493,12 +493,13 @@ int orc_select_parents(const orc_params *pr, uint32_t gen, const int64_t *k1, co
 
 /*
  * Offspring generation (Alg. 1 parallel map, done here one child after the
- * other) and evaluation: Q[i] = mutation(crossover(parents of i)), with keys.
+ * other) and evaluation: Q[i] = mutation(crossover(parents of i)), with keys,
+ * for the children i0 <= i < i1 (Q, qk1, qk2 are indexed by child).
  */
-int orc_make_offspring(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
-                       const orc_params *pr, uint32_t gen, const int32_t *P,
-                       const int64_t *k1, const int64_t *k2,
-                       int32_t *Q, int64_t *qk1, int64_t *qk2)
+int orc_make_offspring_range(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                             const orc_params *pr, uint32_t gen, const int32_t *P,
+                             const int64_t *k1, const int64_t *k2, int32_t i0, int32_t i1,
+                             int32_t *Q, int64_t *qk1, int64_t *qk2)
 {
     int32_t Np = pr->pop_size, E = pr->n_parents;
     orc_graph g = { n, row_ptr, col_idx };
@@ -511,7 +512,9 @@ int orc_make_offspring(int64_t n, const int64_t *row_ptr, const int32_t *col_idx
     if (!par || !xo || !skip || !child) { free(par); free(xo); free(skip); free(child); return ORC_ENOMEM; }
     int rc = orc_select_parents(pr, gen, k1, k2, par, xo, skip);
     uint64_t thr_m = orc_threshold(pr->p_mutation);
-    for (int32_t i = 0; i < Np && rc == ORC_OK; ++i) {
+    if (i0 < 0) i0 = 0;
+    if (i1 > Np) i1 = Np;
+    for (int32_t i = i0; i < i1 && rc == ORC_OK; ++i) {
         for (int32_t j = 0; j < E; ++j) pp[j] = P + (int64_t)par[i * E + j] * n;
         if (xo[i]) rc = crossover_child(n, E, pp, pr->seed, gen, (uint32_t)i, child);
         else memcpy(child, pp[skip[i]], sizeof(int32_t) * (size_t)n);
@@ -525,6 +528,15 @@ int orc_make_offspring(int64_t n, const int64_t *row_ptr, const int32_t *col_idx
     }
     free(par); free(xo); free(skip); free(child);
     return rc;
+}
+
+/* All N_p children of generation gen (the "parallel map" of Alg. 1). */
+int orc_make_offspring(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                       const orc_params *pr, uint32_t gen, const int32_t *P,
+                       const int64_t *k1, const int64_t *k2,
+                       int32_t *Q, int64_t *qk1, int64_t *qk2)
+{
+    return orc_make_offspring_range(n, row_ptr, col_idx, pr, gen, P, k1, k2, 0, pr->pop_size, Q, qk1, qk2);
 }
 
 /*

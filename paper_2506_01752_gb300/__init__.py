@@ -1,0 +1,225 @@
+"""GB300 (sm_103a) engine for HP-MOCD (arXiv 2506.01752): one NSGA-II
+generation of Alg. 1 -- crossover, mutation, evaluation of both objectives and
+environmental selection -- batched over the whole population on one GPU.
+
+This module is a thin ctypes binding of the C ABI in ``include/mocd.h``: it
+only marshals arguments. Every step runs in the CUDA library
+``_build/libmocd.so`` (built by ``paper_2506_01752_gb300.build.build()``); if
+that library is missing, loading fails loudly -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "MocdError", "Params", "Front", "library_path", "load",
+    "graph_upload", "population_init", "generation", "pareto_front",
+    "get_population", "set_population", "evaluate", "synchronize",
+    "set_timing", "kernel_times", "info", "destroy", "status_string",
+    "STAGES",
+]
+
+STAGES = ("crossover", "mutation", "hist_clear", "evaluate", "select")
+
+OK = 0
+ERR_BUFFER_TOO_SMALL = -7
+
+
+class MocdError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+class _CParams(ctypes.Structure):
+    _fields_ = [("pop_size", ctypes.c_int32), ("n_parents", ctypes.c_int32),
+                ("p_crossover", ctypes.c_double), ("p_mutation", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("init_mode", ctypes.c_int32)]
+
+
+@dataclass
+class Params:
+    """Alg. 1 parameters; defaults are the paper's (N_p 100, E_S 4, C_P 0.8, M_P 0.2)."""
+    pop_size: int = 100
+    n_parents: int = 4
+    p_crossover: float = 0.8
+    p_mutation: float = 0.2
+    seed: int = 0
+    init_mode: int = 0
+
+    def _c(self) -> _CParams:
+        return _CParams(self.pop_size, self.n_parents, self.p_crossover, self.p_mutation,
+                        self.seed, self.init_mode)
+
+
+@dataclass
+class Front:
+    """Pareto front F_1 in P order and the recommended member (Alg. 3)."""
+    labels: np.ndarray   # [count][n] int32
+    f1: np.ndarray
+    f2: np.ndarray
+    intra: np.ndarray
+    sumsq: np.ndarray
+    best: int
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load the CUDA library (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} (run paper_2506_01752_gb300.build.build())")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i32, i64 = ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "mocd_graph_upload": (ctypes.c_int, [ctypes.POINTER(P), i64, P, P, P]),
+        "mocd_population_init": (ctypes.c_int, [P, ctypes.POINTER(_CParams)]),
+        "mocd_generation": (ctypes.c_int, [P, i32]),
+        "mocd_pareto_front": (ctypes.c_int, [P, i32, P, P, P, P, P, P, P]),
+        "mocd_get_population": (ctypes.c_int, [P, P, P, P, P]),
+        "mocd_set_population": (ctypes.c_int, [P, ctypes.POINTER(_CParams), P, i32]),
+        "mocd_evaluate": (ctypes.c_int, [P, i32, P, P, P]),
+        "mocd_synchronize": (ctypes.c_int, [P]),
+        "mocd_set_timing": (ctypes.c_int, [P, i32]),
+        "mocd_kernel_times": (ctypes.c_int, [P, P, i32]),
+        "mocd_info": (ctypes.c_int, [P, P, P, P, P]),
+        "mocd_destroy": (None, [P]),
+        "mocd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _p(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise MocdError(rc, what)
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream or None
+    return int(getattr(stream, "cuda_stream")) or None
+
+
+def status_string(status: int) -> str:
+    return load().mocd_status_string(status).decode()
+
+
+def graph_upload(row_ptr, col_idx, stream=None):
+    """Validate and upload a symmetric CSR graph; returns a context handle."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    ctx = ctypes.c_void_p()
+    _check(load().mocd_graph_upload(ctypes.byref(ctx), rp.size - 1, _p(rp), _p(ci),
+                                    _stream_handle(stream)), "mocd_graph_upload")
+    return ctx
+
+
+def population_init(ctx, params: Params):
+    c = params._c()
+    _check(load().mocd_population_init(ctx, ctypes.byref(c)), "mocd_population_init")
+
+
+def generation(ctx, n_generations: int = 1):
+    _check(load().mocd_generation(ctx, int(n_generations)), "mocd_generation")
+
+
+def info(ctx):
+    n = ctypes.c_int64()
+    m = ctypes.c_int64()
+    np_ = ctypes.c_int32()
+    g = ctypes.c_int32()
+    _check(load().mocd_info(ctx, ctypes.byref(n), ctypes.byref(m), ctypes.byref(np_), ctypes.byref(g)),
+           "mocd_info")
+    return dict(n=n.value, m=m.value, pop_size=np_.value, generation=g.value)
+
+
+def pareto_front(ctx, with_labels: bool = True) -> Front:
+    d = info(ctx)
+    n, cap = d["n"], max(d["pop_size"], 1)
+    count = ctypes.c_int32()
+    best = ctypes.c_int32()
+    labels = np.zeros((cap, n), dtype=np.int32) if with_labels else None
+    f1 = np.zeros(cap, dtype=np.float64)
+    f2 = np.zeros(cap, dtype=np.float64)
+    intra = np.zeros(cap, dtype=np.int64)
+    sumsq = np.zeros(cap, dtype=np.int64)
+    _check(load().mocd_pareto_front(ctx, cap, ctypes.byref(count), _p(labels), _p(f1), _p(f2), _p(intra),
+                                    _p(sumsq), ctypes.byref(best)), "mocd_pareto_front")
+    k = count.value
+    return Front(labels[:k] if labels is not None else None, f1[:k], f2[:k], intra[:k], sumsq[:k], best.value)
+
+
+def get_population(ctx):
+    """(labels [N_p][n], k1, k2, generation) of P in P order."""
+    d = info(ctx)
+    labels = np.zeros((d["pop_size"], d["n"]), dtype=np.int32)
+    k1 = np.zeros(d["pop_size"], dtype=np.int64)
+    k2 = np.zeros(d["pop_size"], dtype=np.int64)
+    g = ctypes.c_int32()
+    _check(load().mocd_get_population(ctx, _p(labels), _p(k1), _p(k2), ctypes.byref(g)), "mocd_get_population")
+    return labels, k1, k2, g.value
+
+
+def set_population(ctx, params: Params, labels, generation: int = 0):
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    c = params._c()
+    _check(load().mocd_set_population(ctx, ctypes.byref(c), _p(lab), int(generation)), "mocd_set_population")
+
+
+def evaluate(ctx, labels):
+    """Exact (intra, S) of each labelling in ``labels`` ([count][n])."""
+    lab = np.ascontiguousarray(np.atleast_2d(labels), dtype=np.int32)
+    intra = np.zeros(lab.shape[0], dtype=np.int64)
+    sumsq = np.zeros(lab.shape[0], dtype=np.int64)
+    _check(load().mocd_evaluate(ctx, lab.shape[0], _p(lab), _p(intra), _p(sumsq)), "mocd_evaluate")
+    return intra, sumsq
+
+
+def synchronize(ctx):
+    _check(load().mocd_synchronize(ctx), "mocd_synchronize")
+
+
+def set_timing(ctx, enable: bool):
+    _check(load().mocd_set_timing(ctx, 1 if enable else 0), "mocd_set_timing")
+
+
+def kernel_times(ctx) -> dict:
+    """Milliseconds of each stage of the most recent generation."""
+    ms = np.zeros(len(STAGES), dtype=np.float32)
+    rc = load().mocd_kernel_times(ctx, _p(ms), len(STAGES))
+    if rc < 0:
+        raise MocdError(rc, "mocd_kernel_times")
+    return dict(zip(STAGES, ms.tolist()))
+
+
+def destroy(ctx):
+    if ctx is not None and ctx.value:
+        load().mocd_destroy(ctx)
+        ctx.value = None

@@ -1,0 +1,135 @@
+// k_eval.cu -- objective evaluation of a whole population (Eq. objectives,
+// Sec. 4.1; Alg. 1 EvaluateIndividual, run for every individual at once).
+//
+// For each individual i the kernel accumulates
+//   intra2_i = #{(v, u) : u in N(v), L_i(v) = L_i(u)}   (= 2 sum_c |E(c)|)
+//   S_i      = sum_c D_c^2,  D_c = sum_{v : L_i(v) = c} deg v
+// exactly in integers. Layout is node-major: a warp owns node v and lane q
+// holds the int4 of labels of individuals 4q..4q+3, so each neighbour u costs
+// one coalesced row read of all individuals' labels instead of N_p scattered
+// 4-byte gathers, and the CSR is streamed once per population, not once per
+// individual.
+//
+// S without a sweep over the histogram: when node v adds deg(v) to D_c, the
+// atomic returns the old total o, and (o + d)^2 - o^2 = 2 o d + d^2. Summed
+// over every addition these increments telescope to D_c^2 whatever the order
+// of the atomics, so S is exact and deterministic.
+#include "mocd_internal.h"
+
+namespace mocd {
+
+namespace {
+
+__global__ void __launch_bounds__(kBlock)
+evaluate_kernel(int n, int W, int count, const int32_t *__restrict__ row_ptr,
+                const int32_t *__restrict__ col_idx, const int32_t *__restrict__ labels,
+                uint32_t *__restrict__ hist, unsigned long long *__restrict__ acc)
+{
+    __shared__ unsigned long long s_intra[kMaxPop];
+    __shared__ unsigned long long s_sq[kMaxPop];
+    for (int t = threadIdx.x; t < kMaxPop; t += blockDim.x) {
+        s_intra[t] = 0;
+        s_sq[t] = 0;
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const int nq = W >> 2;
+    const bool active = lane < nq;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int4 *__restrict__ L4 = reinterpret_cast<const int4 *>(labels);
+    const int i0 = 4 * lane;
+
+    uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+    unsigned long long q0 = 0, q1 = 0, q2 = 0, q3 = 0;
+
+    for (int v = warp; v < n; v += nwarps) {
+        const int beg = __ldg(row_ptr + v);
+        const int end = __ldg(row_ptr + v + 1);
+        const int4 own = active ? L4[(size_t)v * nq + lane] : make_int4(0, 0, 0, 0);
+        for (int e0 = beg; e0 < end; e0 += 32) {
+            const int cnt = min(32, end - e0);
+            const int my_u = lane < cnt ? __ldg(col_idx + e0 + lane) : 0;
+            int j = 0;
+            for (; j + 4 <= cnt; j += 4) {
+                const int u0 = __shfl_sync(0xffffffffu, my_u, j);
+                const int u1 = __shfl_sync(0xffffffffu, my_u, j + 1);
+                const int u2 = __shfl_sync(0xffffffffu, my_u, j + 2);
+                const int u3 = __shfl_sync(0xffffffffu, my_u, j + 3);
+                if (active) {
+                    const int4 a = L4[(size_t)u0 * nq + lane];
+                    const int4 b = L4[(size_t)u1 * nq + lane];
+                    const int4 c = L4[(size_t)u2 * nq + lane];
+                    const int4 d = L4[(size_t)u3 * nq + lane];
+                    c0 += (a.x == own.x) + (b.x == own.x) + (c.x == own.x) + (d.x == own.x);
+                    c1 += (a.y == own.y) + (b.y == own.y) + (c.y == own.y) + (d.y == own.y);
+                    c2 += (a.z == own.z) + (b.z == own.z) + (c.z == own.z) + (d.z == own.z);
+                    c3 += (a.w == own.w) + (b.w == own.w) + (c.w == own.w) + (d.w == own.w);
+                }
+            }
+            for (; j < cnt; ++j) {
+                const int u = __shfl_sync(0xffffffffu, my_u, j);
+                if (active) {
+                    const int4 a = L4[(size_t)u * nq + lane];
+                    c0 += a.x == own.x;
+                    c1 += a.y == own.y;
+                    c2 += a.z == own.z;
+                    c3 += a.w == own.w;
+                }
+            }
+        }
+        const unsigned long long d = (unsigned long long)(end - beg);
+        if (active && d > 0) {
+            const unsigned dd = (unsigned)d;
+            if (i0 + 0 < count) {
+                const unsigned long long o = atomicAdd(hist + (size_t)(i0 + 0) * n + own.x, dd);
+                q0 += 2ull * o * d + d * d;
+            }
+            if (i0 + 1 < count) {
+                const unsigned long long o = atomicAdd(hist + (size_t)(i0 + 1) * n + own.y, dd);
+                q1 += 2ull * o * d + d * d;
+            }
+            if (i0 + 2 < count) {
+                const unsigned long long o = atomicAdd(hist + (size_t)(i0 + 2) * n + own.z, dd);
+                q2 += 2ull * o * d + d * d;
+            }
+            if (i0 + 3 < count) {
+                const unsigned long long o = atomicAdd(hist + (size_t)(i0 + 3) * n + own.w, dd);
+                q3 += 2ull * o * d + d * d;
+            }
+        }
+    }
+
+    if (active) {
+        if (i0 + 0 < count) { atomicAdd(&s_intra[i0 + 0], (unsigned long long)c0); atomicAdd(&s_sq[i0 + 0], q0); }
+        if (i0 + 1 < count) { atomicAdd(&s_intra[i0 + 1], (unsigned long long)c1); atomicAdd(&s_sq[i0 + 1], q1); }
+        if (i0 + 2 < count) { atomicAdd(&s_intra[i0 + 2], (unsigned long long)c2); atomicAdd(&s_sq[i0 + 2], q2); }
+        if (i0 + 3 < count) { atomicAdd(&s_intra[i0 + 3], (unsigned long long)c3); atomicAdd(&s_sq[i0 + 3], q3); }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < count; t += blockDim.x) {
+        if (s_intra[t]) atomicAdd(acc + t, s_intra[t]);
+        if (s_sq[t]) atomicAdd(acc + kMaxPop + t, s_sq[t]);
+    }
+}
+
+}  // namespace
+
+int grid_for_eval(int sms)
+{
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, evaluate_kernel, kBlock, 0);
+    if (per_sm < 1) per_sm = 1;
+    return sms * per_sm;
+}
+
+cudaError_t launch_evaluate(int n, int W, int count, const int32_t *row_ptr, const int32_t *col_idx,
+                            const int32_t *labels, uint32_t *hist, unsigned long long *acc,
+                            int grid, cudaStream_t s)
+{
+    evaluate_kernel<<<grid, kBlock, 0, s>>>(n, W, count, row_ptr, col_idx, labels, hist, acc);
+    return cudaGetLastError();
+}
+
+}  // namespace mocd

@@ -1,0 +1,85 @@
+// mocd_internal.h -- declarations shared by the CUDA translation units of the
+// HP-MOCD generation engine (kernels + host runtime). Not part of the C ABI.
+//
+// Device data layout (node-major, "row per node"):
+//   labels   int32 [n][W]   W = pop_size rounded up to a multiple of 4; column i
+//                            of row v is individual i's label of node v, so a
+//                            warp reads a node's labels for every individual
+//                            as one contiguous 16-byte-per-lane row.
+//   hist     uint32 [Np][n] per-individual community degree totals D_c
+//                            (scratch, cleared before every evaluation)
+//   CSR      int32 row_ptr[n + 1], int32 col_idx[2m] (symmetric)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mocd {
+
+constexpr int kMaxPop = 128;      // N_p limit: one int4 of labels per lane per row
+constexpr int kMaxParents = 16;   // E_S limit
+constexpr int kBlock = 256;       // threads per block of the node-parallel kernels
+
+// Random stream stages (third word of the Philox counter is the generation).
+constexpr uint32_t kStageInit = 1;
+constexpr uint32_t kStageSelect = 2;
+constexpr uint32_t kStageCrossTie = 3;
+constexpr uint32_t kStageMutCoin = 4;
+constexpr uint32_t kStageMutTie = 5;
+
+// Per-generation device state of one population.
+struct PopState {
+    int32_t *buf[2];          // P halves [n][W]: the P of R is buf[(g + 1) & 1]
+    int32_t *q;               // Q [n][W]
+    int32_t *c;               // post-crossover children [n][W]
+    uint32_t *hist;           // [Np][n]
+    unsigned long long *acc;  // [2][kMaxPop]: directed intra count, S
+    int64_t *pk;              // [2][kMaxPop]: P keys k1 (m - intra), k2 (S), P order
+    int64_t *rk;              // [2][2 kMaxPop]: R keys (P then Q) of the last selection
+    int32_t *prank;           // [kMaxPop] rank of P on its own keys (1-based)
+    int32_t *keep;            // [kMaxPop] R index of each P position
+    int32_t *par_r;           // [kMaxPop][kMaxParents] parent R indices per child
+    int32_t *copy_r;          // [kMaxPop] R index copied when crossover is skipped, else -1
+    uint32_t *gen;            // next generation number to run (device counter)
+    int32_t *front;           // [2 + kMaxPop]: count, best, members (P positions)
+    int64_t *fint;            // [2][kMaxPop]: intra, S of each front member
+    double *fval;             // [2][kMaxPop]: f1, f2 of each front member
+};
+
+struct GenParams {
+    int n;                    // nodes
+    int W;                    // row width (ints)
+    int np;                   // N_p
+    int es;                   // E_S
+    int label_bits;           // bits needed for a label in [0, n)
+    int hash_size;            // per-warp hash entries for degree > 32 (0: none)
+    int64_t m;                // edges
+    uint32_t key0, key1;      // Philox key (seed)
+    unsigned long long thr_c; // crossover iff u <= thr_c
+    unsigned long long thr_m; // mutate iff u < thr_m
+};
+
+// Launch wrappers (stream-ordered, return cudaGetLastError()).
+cudaError_t launch_init_population(const GenParams &gp, int32_t *dst, cudaStream_t s);
+cudaError_t launch_crossover(const GenParams &gp, const PopState &ps, int grid, cudaStream_t s);
+cudaError_t launch_mutation(const GenParams &gp, const PopState &ps, const int32_t *row_ptr,
+                            const int32_t *col_idx, int grid, cudaStream_t s);
+cudaError_t launch_evaluate(int n, int W, int count, const int32_t *row_ptr, const int32_t *col_idx,
+                            const int32_t *labels, uint32_t *hist, unsigned long long *acc,
+                            int grid, cudaStream_t s);
+// mode 0: keys of a fresh P from acc, keep = identity; mode 1: R = P u Q,
+// environmental selection. Both then rank P and draw the next tournament.
+cudaError_t launch_select(const GenParams &gp, const PopState &ps, int mode, cudaStream_t s);
+cudaError_t launch_front(const GenParams &gp, const PopState &ps, cudaStream_t s);
+// out[k][v] = R_v[idx[k]] for k < count, R_v = (phalf row v | q row v); idx NULL: identity on phalf.
+cudaError_t launch_gather_individuals(int n, int W, int np, const int32_t *phalf, const int32_t *q,
+                                      const int32_t *idx, int count, int32_t *out, cudaStream_t s);
+// dst[v][k] = src[k][v] for k < count, zero for count <= k < W.
+cudaError_t launch_to_node_major(int n, int W, int count, const int32_t *src, int32_t *dst,
+                                 cudaStream_t s);
+// Occupancy-derived grid sizes.
+int grid_for_eval(int sms);
+int grid_for_crossover(int sms, int es);
+int grid_for_mutation(int sms, int hash_size, int *smem_bytes);
+
+}  // namespace mocd

@@ -1,0 +1,623 @@
+// runtime.cu -- host side of the C ABI declared in include/mocd.h.
+//
+// A context owns the uploaded CSR, the population buffers (node-major label
+// rows, see mocd_internal.h) and one CUDA graph that runs a whole generation
+// of Alg. 1: crossover -> mutation -> clear histogram -> evaluate -> select.
+// Every kernel reads the generation number from device memory, so the same
+// graph is replayed for every generation with no host work in between.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mocd.h"
+#include "mocd_internal.h"
+
+using namespace mocd;
+
+namespace {
+
+constexpr int kStages = 5;
+
+}  // namespace
+
+struct mocd_ctx {
+    int device = 0;
+    int sms = 1;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+
+    int64_t n = 0, m = 0;
+    int dmax = 0;
+    int32_t *d_row_ptr = nullptr;
+    int32_t *d_col_idx = nullptr;
+
+    // Population.
+    bool ready = false;
+    mocd_params params{};
+    GenParams gp{};
+    PopState ps{};
+    int W = 0;
+    size_t pop_cells = 0;   // n * W of the allocated label buffers
+    size_t hist_cap = 0;    // entries of ps.hist
+    void *d_small = nullptr;
+    int grid_eval = 0, grid_cross = 0, grid_mut = 0;
+    int32_t host_gen = 0;   // generations run since init
+    uint32_t gen_host_value = 0;
+
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    bool timing = false;
+    bool timing_valid = false;
+    cudaEvent_t ev[kStages + 1] = {};
+
+    // Scratch for downloads and for mocd_evaluate.
+    int32_t *d_im = nullptr;   // individual-major [rows][n]
+    size_t im_cap = 0;
+    int32_t *d_nm = nullptr;   // node-major [n][128]
+    size_t nm_cap = 0;
+    unsigned long long *d_eval_acc = nullptr;
+    uint32_t *d_eval_hist = nullptr;
+    size_t eval_hist_cap = 0;
+    int32_t *d_idx = nullptr;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return MOCD_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return MOCD_ERR_OUT_OF_MEMORY;
+    }
+    return MOCD_ERR_CUDA;
+}
+
+#define CK(call)                                      \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return cuda_status(e_);\
+    } while (0)
+
+template <class T>
+int grow(T **p, size_t *cap, size_t need)
+{
+    if (*p && *cap >= need) return MOCD_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(need, 1) * sizeof(T));
+    if (e != cudaSuccess) return cuda_status(e);
+    *p = static_cast<T *>(q);
+    *cap = need;
+    return MOCD_OK;
+}
+
+void free_population(mocd_ctx *c)
+{
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+    cudaFree(c->ps.buf[0]);
+    cudaFree(c->ps.buf[1]);
+    cudaFree(c->ps.q);
+    cudaFree(c->ps.c);
+    cudaFree(c->ps.hist);
+    cudaFree(c->d_small);
+    c->ps = PopState{};
+    c->d_small = nullptr;
+    c->pop_cells = 0;
+    c->hist_cap = 0;
+    c->ready = false;
+}
+
+int label_bits_for(int64_t n)
+{
+    int b = 0;
+    while ((int64_t(1) << b) < n) ++b;
+    return b;
+}
+
+int check_params(const mocd_ctx *c, const mocd_params *p)
+{
+    if (!p) return MOCD_ERR_INVALID_ARG;
+    if (p->pop_size < 1 || p->pop_size > kMaxPop) return MOCD_ERR_INVALID_ARG;
+    if (p->n_parents < 1 || p->n_parents > kMaxParents) return MOCD_ERR_INVALID_ARG;
+    if (!(p->p_crossover >= 0.0 && p->p_crossover <= 1.0)) return MOCD_ERR_INVALID_ARG;
+    if (!(p->p_mutation >= 0.0 && p->p_mutation <= 1.0)) return MOCD_ERR_INVALID_ARG;
+    if (p->init_mode != 0) return MOCD_ERR_INVALID_ARG;
+    if (c->dmax > 512) return MOCD_ERR_INVALID_ARG;  // mutation count table limit
+    return MOCD_OK;
+}
+
+// Allocate (or reuse) the population buffers for params and fill gp / ps.
+int prepare_population(mocd_ctx *c, const mocd_params *p)
+{
+    const int W = (p->pop_size + 3) & ~3;
+    const size_t cells = (size_t)c->n * (size_t)W;
+    if (c->ready || c->graph_exec) {
+        if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+        if (c->graph) cudaGraphDestroy(c->graph);
+        c->graph_exec = nullptr;
+        c->graph = nullptr;
+    }
+    if (c->pop_cells != cells) {
+        free_population(c);
+        int32_t *b[4] = {};
+        for (int k = 0; k < 4; ++k) {
+            void *q = nullptr;
+            cudaError_t e = cudaMalloc(&q, cells * sizeof(int32_t));
+            if (e != cudaSuccess) {
+                for (int j = 0; j < k; ++j) cudaFree(b[j]);
+                return cuda_status(e);
+            }
+            b[k] = static_cast<int32_t *>(q);
+        }
+        c->ps.buf[0] = b[0];
+        c->ps.buf[1] = b[1];
+        c->ps.q = b[2];
+        c->ps.c = b[3];
+        c->pop_cells = cells;
+        // Small per-generation state in one allocation.
+        const size_t bytes = sizeof(unsigned long long) * 2 * kMaxPop   // acc
+                             + sizeof(int64_t) * 2 * kMaxPop              // pk
+                             + sizeof(int64_t) * 4 * kMaxPop              // rk
+                             + sizeof(int32_t) * kMaxPop                  // prank
+                             + sizeof(int32_t) * kMaxPop                  // keep
+                             + sizeof(int32_t) * kMaxPop * kMaxParents    // par_r
+                             + sizeof(int32_t) * kMaxPop                  // copy_r
+                             + sizeof(int32_t) * (2 + kMaxPop)            // front
+                             + sizeof(int64_t) * 2 * kMaxPop              // fint
+                             + sizeof(double) * 2 * kMaxPop               // fval
+                             + 64;                                        // gen, alignment
+        void *s = nullptr;
+        cudaError_t e = cudaMalloc(&s, bytes);
+        if (e != cudaSuccess) return cuda_status(e);
+        c->d_small = s;
+        char *q = static_cast<char *>(s);
+        c->ps.acc = reinterpret_cast<unsigned long long *>(q); q += sizeof(unsigned long long) * 2 * kMaxPop;
+        c->ps.pk = reinterpret_cast<int64_t *>(q); q += sizeof(int64_t) * 2 * kMaxPop;
+        c->ps.rk = reinterpret_cast<int64_t *>(q); q += sizeof(int64_t) * 4 * kMaxPop;
+        c->ps.prank = reinterpret_cast<int32_t *>(q); q += sizeof(int32_t) * kMaxPop;
+        c->ps.keep = reinterpret_cast<int32_t *>(q); q += sizeof(int32_t) * kMaxPop;
+        c->ps.par_r = reinterpret_cast<int32_t *>(q); q += sizeof(int32_t) * kMaxPop * kMaxParents;
+        c->ps.copy_r = reinterpret_cast<int32_t *>(q); q += sizeof(int32_t) * kMaxPop;
+        c->ps.front = reinterpret_cast<int32_t *>(q); q += sizeof(int32_t) * (2 + kMaxPop);
+        q = reinterpret_cast<char *>((reinterpret_cast<uintptr_t>(q) + 15) & ~uintptr_t(15));
+        c->ps.fint = reinterpret_cast<int64_t *>(q); q += sizeof(int64_t) * 2 * kMaxPop;
+        c->ps.fval = reinterpret_cast<double *>(q); q += sizeof(double) * 2 * kMaxPop;
+        c->ps.gen = reinterpret_cast<uint32_t *>(q);
+        CK(cudaMemsetAsync(s, 0, bytes, c->stream));
+        CK(cudaMemsetAsync(c->ps.q, 0, cells * sizeof(int32_t), c->stream));
+        CK(cudaMemsetAsync(c->ps.buf[0], 0, cells * sizeof(int32_t), c->stream));
+    }
+    const size_t hist_need = (size_t)p->pop_size * (size_t)c->n;
+    {
+        int rc = grow(&c->ps.hist, &c->hist_cap, hist_need);
+        if (rc) return rc;
+    }
+    c->W = W;
+    c->params = *p;
+    GenParams &gp = c->gp;
+    gp.n = (int)c->n;
+    gp.W = W;
+    gp.np = p->pop_size;
+    gp.es = p->n_parents;
+    gp.label_bits = label_bits_for(c->n);
+    int hs = 0;
+    if (c->dmax > 32) {
+        hs = 128;
+        while (hs < 2 * c->dmax) hs <<= 1;
+    }
+    gp.hash_size = hs;
+    gp.m = c->m;
+    gp.key0 = (uint32_t)p->seed;
+    gp.key1 = (uint32_t)(p->seed >> 32);
+    gp.thr_c = (unsigned long long)floor(p->p_crossover * 4294967296.0);
+    gp.thr_m = (unsigned long long)floor(p->p_mutation * 4294967296.0);
+    c->grid_eval = grid_for_eval(c->sms);
+    c->grid_cross = grid_for_crossover(c->sms, gp.es);
+    int smem = 0;
+    c->grid_mut = grid_for_mutation(c->sms, gp.hash_size, &smem);
+    return MOCD_OK;
+}
+
+int clear_eval_state(mocd_ctx *c, uint32_t *hist, size_t hist_entries, unsigned long long *acc)
+{
+    CK(cudaMemsetAsync(hist, 0, hist_entries * sizeof(uint32_t), c->stream));
+    CK(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 2 * kMaxPop, c->stream));
+    return MOCD_OK;
+}
+
+// Timing events become event-record nodes of the captured graph.
+cudaError_t mark(mocd_ctx *c, int k)
+{
+    return cudaEventRecordWithFlags(c->ev[k], c->stream, cudaEventRecordExternal);
+}
+
+// One generation of Alg. 1 on the context stream.
+int issue_generation(mocd_ctx *c, bool events)
+{
+    const GenParams &gp = c->gp;
+    const PopState &ps = c->ps;
+    if (events) CK(mark(c, 0));
+    CK(launch_crossover(gp, ps, c->grid_cross, c->stream));
+    if (events) CK(mark(c, 1));
+    CK(launch_mutation(gp, ps, c->d_row_ptr, c->d_col_idx, c->grid_mut, c->stream));
+    if (events) CK(mark(c, 2));
+    int rc = clear_eval_state(c, ps.hist, (size_t)gp.np * (size_t)gp.n, ps.acc);
+    if (rc) return rc;
+    if (events) CK(mark(c, 3));
+    CK(launch_evaluate(gp.n, gp.W, gp.np, c->d_row_ptr, c->d_col_idx, ps.q, ps.hist, ps.acc,
+                       c->grid_eval, c->stream));
+    if (events) CK(mark(c, 4));
+    CK(launch_select(gp, ps, 1, c->stream));
+    if (events) CK(mark(c, 5));
+    return MOCD_OK;
+}
+
+int build_graph(mocd_ctx *c)
+{
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+    c->graph = nullptr;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = issue_generation(c, c->timing);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    CK(e);
+    c->graph = g;
+    CK(cudaGraphInstantiate(&c->graph_exec, g, 0));
+    return MOCD_OK;
+}
+
+// Evaluate, rank and draw the first tournament of a population whose labels
+// are in the P half of generation base_gen (buf[(base_gen + 1) & 1]).
+int start_population(mocd_ctx *c, uint32_t base_gen)
+{
+    const GenParams &gp = c->gp;
+    PopState &ps = c->ps;
+    int32_t *phalf = ps.buf[(base_gen + 1u) & 1u];
+    int rc = clear_eval_state(c, ps.hist, (size_t)gp.np * (size_t)gp.n, ps.acc);
+    if (rc) return rc;
+    CK(launch_evaluate(gp.n, gp.W, gp.np, c->d_row_ptr, c->d_col_idx, phalf, ps.hist, ps.acc,
+                       c->grid_eval, c->stream));
+    c->gen_host_value = base_gen;
+    CK(cudaMemcpyAsync(ps.gen, &c->gen_host_value, sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream));
+    CK(launch_select(gp, ps, 0, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->host_gen = (int32_t)base_gen;
+    rc = build_graph(c);
+    if (rc) return rc;
+    c->ready = true;
+    c->timing_valid = false;
+    return MOCD_OK;
+}
+
+int validate_labels(const mocd_ctx *c, const int32_t *labels, size_t count)
+{
+    const int32_t n = (int32_t)c->n;
+    for (size_t k = 0; k < count; ++k)
+        if (labels[k] < 0 || labels[k] >= n) return MOCD_ERR_INVALID_ARG;
+    return MOCD_OK;
+}
+
+// Individual-major labels of `count` P positions (pos NULL: all of P).
+int download_members(mocd_ctx *c, const int32_t *pos_host, int count, int32_t *labels)
+{
+    if (count <= 0 || !labels) return MOCD_OK;
+    int rc = grow(&c->d_im, &c->im_cap, (size_t)count * (size_t)c->n);
+    if (rc) return rc;
+    std::vector<int32_t> keep(c->gp.np);
+    CK(cudaMemcpyAsync(keep.data(), c->ps.keep, sizeof(int32_t) * c->gp.np, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    std::vector<int32_t> ridx(count);
+    for (int k = 0; k < count; ++k) ridx[k] = keep[pos_host ? pos_host[k] : k];
+    if (!c->d_idx) {
+        void *q = nullptr;
+        CK(cudaMalloc(&q, sizeof(int32_t) * kMaxPop));
+        c->d_idx = static_cast<int32_t *>(q);
+    }
+    CK(cudaMemcpyAsync(c->d_idx, ridx.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, c->stream));
+    const int32_t *phalf = c->ps.buf[(uint32_t)(c->host_gen + 1) & 1u];
+    CK(launch_gather_individuals((int)c->n, c->W, c->gp.np, phalf, c->ps.q, c->d_idx, count, c->d_im,
+                                 c->stream));
+    CK(cudaMemcpyAsync(labels, c->d_im, sizeof(int32_t) * (size_t)count * (size_t)c->n,
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return MOCD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mocd_status_string(int status)
+{
+    switch (status) {
+    case MOCD_OK: return "ok";
+    case MOCD_ERR_INVALID_ARG: return "invalid argument";
+    case MOCD_ERR_NOT_SYMMETRIC: return "adjacency is not symmetric";
+    case MOCD_ERR_SELF_LOOP: return "self loop";
+    case MOCD_ERR_DUPLICATE_EDGE: return "repeated edge";
+    case MOCD_ERR_EMPTY_GRAPH: return "graph has no edges";
+    case MOCD_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case MOCD_ERR_BUFFER_TOO_SMALL: return "output buffer too small";
+    case MOCD_ERR_CUDA: return "CUDA error";
+    case MOCD_ERR_NOT_READY: return "population not initialised";
+    default: return "unknown status";
+    }
+}
+
+int mocd_graph_upload(mocd_ctx **out, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                      void *cuda_stream)
+{
+    if (!out) return MOCD_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!row_ptr || n < 1 || n >= (int64_t(1) << 30)) return MOCD_ERR_INVALID_ARG;
+    if (row_ptr[0] != 0) return MOCD_ERR_INVALID_ARG;
+    for (int64_t v = 0; v < n; ++v)
+        if (row_ptr[v + 1] < row_ptr[v]) return MOCD_ERR_INVALID_ARG;
+    const int64_t nnz = row_ptr[n];
+    if (nnz >= (int64_t(1) << 31)) return MOCD_ERR_INVALID_ARG;
+    if (nnz > 0 && !col_idx) return MOCD_ERR_INVALID_ARG;
+    // Sorted copy of every adjacency list: self loops, repeats, symmetry.
+    std::vector<int32_t> adj(col_idx, col_idx + nnz);
+    int dmax = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        int32_t *b = adj.data() + row_ptr[v], *e = adj.data() + row_ptr[v + 1];
+        std::sort(b, e);
+        dmax = std::max<int>(dmax, (int)(e - b));
+        for (int32_t *p = b; p < e; ++p) {
+            if (*p < 0 || *p >= n) return MOCD_ERR_INVALID_ARG;
+            if (*p == v) return MOCD_ERR_SELF_LOOP;
+            if (p > b && p[-1] == *p) return MOCD_ERR_DUPLICATE_EDGE;
+        }
+    }
+    for (int64_t v = 0; v < n; ++v) {
+        for (int64_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
+            const int32_t u = adj[k];
+            if (!std::binary_search(adj.data() + row_ptr[u], adj.data() + row_ptr[u + 1], (int32_t)v))
+                return MOCD_ERR_NOT_SYMMETRIC;
+        }
+    }
+    if (nnz == 0) return MOCD_ERR_EMPTY_GRAPH;
+
+    mocd_ctx *c = new (std::nothrow) mocd_ctx();
+    if (!c) return MOCD_ERR_OUT_OF_MEMORY;
+    auto fail = [&](int rc) {
+        mocd_destroy(c);
+        return rc;
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess) return fail(MOCD_ERR_CUDA);
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (cuda_stream) {
+        c->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(MOCD_ERR_CUDA);
+        c->own_stream = true;
+    }
+    for (int k = 0; k <= kStages; ++k)
+        if (cudaEventCreate(&c->ev[k]) != cudaSuccess) return fail(MOCD_ERR_CUDA);
+    c->n = n;
+    c->m = nnz / 2;
+    c->dmax = dmax;
+    std::vector<int32_t> rp32(n + 1);
+    for (int64_t v = 0; v <= n; ++v) rp32[v] = (int32_t)row_ptr[v];
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, sizeof(int32_t) * (n + 1));
+    if (e != cudaSuccess) return fail(cuda_status(e));
+    c->d_row_ptr = static_cast<int32_t *>(p);
+    e = cudaMalloc(&p, sizeof(int32_t) * nnz);
+    if (e != cudaSuccess) return fail(cuda_status(e));
+    c->d_col_idx = static_cast<int32_t *>(p);
+    if (cudaMemcpyAsync(c->d_row_ptr, rp32.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice,
+                        c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(c->d_col_idx, adj.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice,
+                        c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return fail(MOCD_ERR_CUDA);
+    *out = c;
+    return MOCD_OK;
+}
+
+int mocd_population_init(mocd_ctx *c, const mocd_params *params)
+{
+    if (!c) return MOCD_ERR_INVALID_ARG;
+    int rc = check_params(c, params);
+    if (rc) return rc;
+    CK(cudaSetDevice(c->device));
+    rc = prepare_population(c, params);
+    if (rc) return rc;
+    CK(launch_init_population(c->gp, c->ps.buf[1], c->stream));
+    return start_population(c, 0);
+}
+
+int mocd_set_population(mocd_ctx *c, const mocd_params *params, const int32_t *labels, int32_t generation)
+{
+    if (!c || !labels || generation < 0) return MOCD_ERR_INVALID_ARG;
+    int rc = check_params(c, params);
+    if (rc) return rc;
+    rc = validate_labels(c, labels, (size_t)params->pop_size * (size_t)c->n);
+    if (rc) return rc;
+    CK(cudaSetDevice(c->device));
+    rc = prepare_population(c, params);
+    if (rc) return rc;
+    rc = grow(&c->d_im, &c->im_cap, (size_t)params->pop_size * (size_t)c->n);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(c->d_im, labels, sizeof(int32_t) * (size_t)params->pop_size * (size_t)c->n,
+                       cudaMemcpyHostToDevice, c->stream));
+    int32_t *phalf = c->ps.buf[((uint32_t)generation + 1u) & 1u];
+    CK(launch_to_node_major((int)c->n, c->W, params->pop_size, c->d_im, phalf, c->stream));
+    return start_population(c, (uint32_t)generation);
+}
+
+int mocd_generation(mocd_ctx *c, int32_t n_generations)
+{
+    if (!c || n_generations < 0) return MOCD_ERR_INVALID_ARG;
+    if (!c->ready) return MOCD_ERR_NOT_READY;
+    for (int32_t k = 0; k < n_generations; ++k) CK(cudaGraphLaunch(c->graph_exec, c->stream));
+    c->host_gen += n_generations;
+    if (n_generations > 0 && c->timing) c->timing_valid = true;
+    return MOCD_OK;
+}
+
+int mocd_pareto_front(mocd_ctx *c, int32_t cap, int32_t *count, int32_t *labels, double *f1, double *f2,
+                      int64_t *intra, int64_t *sumsq, int32_t *best)
+{
+    if (!c || !count || cap < 0) return MOCD_ERR_INVALID_ARG;
+    if (!c->ready) return MOCD_ERR_NOT_READY;
+    CK(cudaSetDevice(c->device));
+    const int np = c->gp.np;
+    CK(launch_front(c->gp, c->ps, c->stream));
+    std::vector<int32_t> fr(2 + np);
+    std::vector<int64_t> fint(2 * kMaxPop);
+    std::vector<double> fval(2 * kMaxPop);
+    CK(cudaMemcpyAsync(fr.data(), c->ps.front, sizeof(int32_t) * (2 + np), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(fint.data(), c->ps.fint, sizeof(int64_t) * 2 * kMaxPop, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(fval.data(), c->ps.fval, sizeof(double) * 2 * kMaxPop, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const int cnt = fr[0];
+    *count = cnt;
+    if (cnt > cap) return MOCD_ERR_BUFFER_TOO_SMALL;
+    if (best) *best = fr[1];
+    const int32_t *members = fr.data() + 2;
+    for (int k = 0; k < cnt; ++k) {
+        if (intra) intra[k] = fint[k];
+        if (sumsq) sumsq[k] = fint[kMaxPop + k];
+        if (f1) f1[k] = fval[k];
+        if (f2) f2[k] = fval[kMaxPop + k];
+    }
+    return download_members(c, members, cnt, labels);
+}
+
+int mocd_get_population(mocd_ctx *c, int32_t *labels, int64_t *k1, int64_t *k2, int32_t *generation)
+{
+    if (!c) return MOCD_ERR_INVALID_ARG;
+    if (!c->ready) return MOCD_ERR_NOT_READY;
+    CK(cudaSetDevice(c->device));
+    const int np = c->gp.np;
+    std::vector<int64_t> pk(2 * kMaxPop);
+    CK(cudaMemcpyAsync(pk.data(), c->ps.pk, sizeof(int64_t) * 2 * kMaxPop, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < np; ++k) {
+        if (k1) k1[k] = pk[k];
+        if (k2) k2[k] = pk[kMaxPop + k];
+    }
+    if (generation) *generation = c->host_gen;
+    return download_members(c, nullptr, np, labels);
+}
+
+int mocd_evaluate(mocd_ctx *c, int32_t count, const int32_t *labels, int64_t *intra, int64_t *sumsq)
+{
+    if (!c || count < 0) return MOCD_ERR_INVALID_ARG;
+    if (count == 0) return MOCD_OK;
+    if (!labels || !intra || !sumsq) return MOCD_ERR_INVALID_ARG;
+    int rc = validate_labels(c, labels, (size_t)count * (size_t)c->n);
+    if (rc) return rc;
+    CK(cudaSetDevice(c->device));
+    const int batch = std::min<int>(count, kMaxPop);
+    const size_t n = (size_t)c->n;
+    if ((rc = grow(&c->d_im, &c->im_cap, (size_t)batch * n))) return rc;
+    if ((rc = grow(&c->d_nm, &c->nm_cap, (size_t)kMaxPop * n))) return rc;
+    if ((rc = grow(&c->d_eval_hist, &c->eval_hist_cap, (size_t)batch * n))) return rc;
+    if (!c->d_eval_acc) {
+        void *q = nullptr;
+        CK(cudaMalloc(&q, sizeof(unsigned long long) * 2 * kMaxPop));
+        c->d_eval_acc = static_cast<unsigned long long *>(q);
+    }
+    const int grid = grid_for_eval(c->sms);
+    std::vector<unsigned long long> acc(2 * kMaxPop);
+    for (int b0 = 0; b0 < count; b0 += batch) {
+        const int b = std::min(batch, count - b0);
+        const int W = (b + 3) & ~3;
+        CK(cudaMemcpyAsync(c->d_im, labels + (size_t)b0 * n, sizeof(int32_t) * (size_t)b * n,
+                           cudaMemcpyHostToDevice, c->stream));
+        CK(launch_to_node_major((int)n, W, b, c->d_im, c->d_nm, c->stream));
+        if ((rc = clear_eval_state(c, c->d_eval_hist, (size_t)b * n, c->d_eval_acc))) return rc;
+        CK(launch_evaluate((int)n, W, b, c->d_row_ptr, c->d_col_idx, c->d_nm, c->d_eval_hist, c->d_eval_acc,
+                           grid, c->stream));
+        CK(cudaMemcpyAsync(acc.data(), c->d_eval_acc, sizeof(unsigned long long) * 2 * kMaxPop,
+                           cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (int k = 0; k < b; ++k) {
+            intra[b0 + k] = (int64_t)(acc[k] / 2ull);
+            sumsq[b0 + k] = (int64_t)acc[kMaxPop + k];
+        }
+    }
+    return MOCD_OK;
+}
+
+int mocd_synchronize(mocd_ctx *c)
+{
+    if (!c) return MOCD_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(c->stream));
+    return MOCD_OK;
+}
+
+int mocd_set_timing(mocd_ctx *c, int32_t enable)
+{
+    if (!c) return MOCD_ERR_INVALID_ARG;
+    const bool want = enable != 0;
+    if (want == c->timing) return MOCD_OK;
+    c->timing = want;
+    c->timing_valid = false;
+    if (c->ready) {
+        CK(cudaStreamSynchronize(c->stream));
+        return build_graph(c);
+    }
+    return MOCD_OK;
+}
+
+int mocd_kernel_times(mocd_ctx *c, float *ms, int32_t cap)
+{
+    if (!c || !ms || cap < kStages) return MOCD_ERR_INVALID_ARG;
+    if (!c->timing || !c->timing_valid) return MOCD_ERR_NOT_READY;
+    CK(cudaEventSynchronize(c->ev[kStages]));
+    for (int k = 0; k < kStages; ++k) CK(cudaEventElapsedTime(ms + k, c->ev[k], c->ev[k + 1]));
+    return kStages;
+}
+
+int mocd_info(mocd_ctx *c, int64_t *n, int64_t *m, int32_t *pop_size, int32_t *generation)
+{
+    if (!c) return MOCD_ERR_INVALID_ARG;
+    if (n) *n = c->n;
+    if (m) *m = c->m;
+    if (pop_size) *pop_size = c->ready ? c->gp.np : 0;
+    if (generation) *generation = c->host_gen;
+    return MOCD_OK;
+}
+
+void mocd_destroy(mocd_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_population(c);
+    cudaFree(c->d_row_ptr);
+    cudaFree(c->d_col_idx);
+    cudaFree(c->d_im);
+    cudaFree(c->d_nm);
+    cudaFree(c->d_eval_acc);
+    cudaFree(c->d_idx);
+    cudaFree(c->d_eval_hist);
+    for (int k = 0; k <= kStages; ++k)
+        if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,247 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the CPU
+oracle on the same seeded inputs. Everything here is integer or a single IEEE
+division per value, so the bar is bit-exact equality: labels, integer keys
+(m - intra, S), f1/f2 doubles, front membership and the recommended member.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2506_01752_gb300 as mocd
+import synth
+from _golden import graph, ints, load
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    mocd.build.build()
+    mocd.load()
+    oracle.build()
+
+
+class Ctx:
+    def __init__(self, rp, ci):
+        self.rp, self.ci = rp, ci
+        self.h = mocd.graph_upload(rp, ci)
+
+    def __enter__(self):
+        return self.h
+
+    def __exit__(self, *a):
+        mocd.destroy(self.h)
+
+
+def star_plus(n_leaves=300, extra=40, seed=0):
+    """A hub of degree n_leaves (> 32, the count-table path) plus a random
+    sparse part and isolated nodes (degree 0)."""
+    rng = np.random.default_rng(seed)
+    n = n_leaves + 1 + extra + 5
+    u = [0] * n_leaves
+    v = list(range(1, n_leaves + 1))
+    a = rng.integers(1, n - 5, 600)
+    b = rng.integers(1, n - 5, 600)
+    rp, ci = synth.csr_from_edges(n, np.concatenate([u, a]), np.concatenate([v, b]))
+    return rp, ci
+
+
+GRAPHS = {
+    "fig2": lambda: graph(load("fig2_toy_graph.txt")),
+    "appE": lambda: graph(load("appE_operator_example.txt")),
+    "planted-1k": lambda: synth.workload("planted-1k", seed=0)[:2],
+    "lfr-3k": lambda: synth.lfr_style(3000, 20, 50, 0.3, seed=2)[:2],
+    "star": lambda: star_plus(),
+    "pair": lambda: synth.csr_from_edges(2, [0], [1]),
+}
+
+
+@pytest.mark.parametrize("gname", list(GRAPHS))
+@pytest.mark.parametrize("kind", ["uniform", "few", "one", "singletons"])
+def test_evaluate_matches_oracle(gname, kind):
+    rp, ci = GRAPHS[gname]()
+    n = rp.size - 1
+    if kind == "uniform":
+        lab = synth.random_labels(n, 7, seed=3)
+    elif kind == "few":
+        lab = synth.random_labels(n, 5, seed=4, n_distinct=min(n, 6))
+    elif kind == "one":
+        lab = np.full((1, n), n - 1, np.int32)
+    else:
+        lab = np.arange(n, dtype=np.int32)[None, :]
+    with Ctx(rp, ci) as h:
+        gi, gs = mocd.evaluate(h, lab)
+    oi, os_ = oracle.objectives(rp, ci, lab)
+    assert np.array_equal(gi, oi) and np.array_equal(gs, os_)
+
+
+def test_evaluate_large_batches_and_lfr_40k():
+    rp, ci, _ = synth.workload("lfr-40k", seed=0)
+    n = rp.size - 1
+    lab = np.concatenate([synth.random_labels(n, 70, seed=5),
+                          synth.random_labels(n, 70, seed=6, n_distinct=900)])  # 140 > one batch of 128
+    with Ctx(rp, ci) as h:
+        gi, gs = mocd.evaluate(h, lab)
+    oi, os_ = oracle.objectives(rp, ci, lab)
+    assert np.array_equal(gi, oi) and np.array_equal(gs, os_)
+
+
+def test_evaluate_rejects_out_of_range():
+    rp, ci = GRAPHS["planted-1k"]()
+    n = rp.size - 1
+    lab = np.zeros((2, n), np.int32)
+    lab[1, 5] = n
+    with Ctx(rp, ci) as h:
+        with pytest.raises(mocd.MocdError) as e:
+            mocd.evaluate(h, lab)
+        assert e.value.status == -1
+
+
+def _params(**kw):
+    return mocd.Params(**kw), oracle.Params(**kw)
+
+
+def _compare_state(h, ref, m):
+    labels, k1, k2, gen = mocd.get_population(h)
+    assert gen == ref.generation
+    assert np.array_equal(k1, ref.k1), "k1 differs"
+    assert np.array_equal(k2, ref.k2), "k2 differs"
+    assert np.array_equal(labels, ref.labels), "labels differ"
+    fr = mocd.pareto_front(h)
+    members, best = oracle.pareto_front(ref, m)
+    assert fr.best == best
+    assert np.array_equal(fr.labels, ref.labels[members])
+    assert np.array_equal(fr.intra, m - ref.k1[members]) and np.array_equal(fr.sumsq, ref.k2[members])
+    for a in range(members.size):
+        f1, f2 = oracle.objective_values(m, int(ref.k1[members[a]]), int(ref.k2[members[a]]))
+        assert fr.f1[a] == f1 and fr.f2[a] == f2
+
+
+@pytest.mark.parametrize("gname", ["fig2", "appE", "pair", "star", "planted-1k"])
+def test_init_matches_oracle(gname):
+    rp, ci = GRAPHS[gname]()
+    gp, op = _params(pop_size=37, seed=11)
+    with Ctx(rp, ci) as h:
+        mocd.population_init(h, gp)
+        _compare_state(h, oracle.population_init(rp, ci, op), int(rp[-1] // 2))
+
+
+@pytest.mark.parametrize("gname,G,kw", [
+    ("appE", 6, dict(pop_size=8)),
+    ("fig2", 6, dict(pop_size=13, n_parents=3)),
+    ("pair", 4, dict(pop_size=5)),
+    ("star", 4, dict(pop_size=24)),
+    ("star", 3, dict(pop_size=16, p_mutation=1.0)),
+    ("planted-1k", 5, dict(pop_size=100)),
+    ("planted-1k", 3, dict(pop_size=128, n_parents=16)),
+    ("planted-1k", 3, dict(pop_size=1)),
+    ("planted-1k", 3, dict(pop_size=2, n_parents=1)),
+    ("planted-1k", 3, dict(pop_size=33, n_parents=5, p_crossover=1.0, p_mutation=0.0)),
+    ("planted-1k", 3, dict(pop_size=31, n_parents=8, p_crossover=0.0, p_mutation=1.0)),
+    ("lfr-3k", 4, dict(pop_size=100, seed=5)),
+])
+def test_generations_match_oracle(gname, G, kw):
+    rp, ci = GRAPHS[gname]()
+    gp, op = _params(**kw)
+    m = int(rp[-1] // 2)
+    ref = oracle.population_init(rp, ci, op)
+    with Ctx(rp, ci) as h:
+        mocd.population_init(h, gp)
+        for step in range(G):
+            mocd.generation(h, 1)
+            ref = oracle.run(rp, ci, op, ref, 1)
+            _compare_state(h, ref, m)
+
+
+def test_planted_full_run_front_bit_exact():
+    """The tiny workload: planted partition n = 1000, N_p = 100, G = 100."""
+    rp, ci, truth = synth.workload("planted-1k", seed=0)
+    gp, op = _params(seed=0)
+    m = int(rp[-1] // 2)
+    with Ctx(rp, ci) as h:
+        mocd.population_init(h, gp)
+        mocd.generation(h, 100)
+        ref = oracle.run(rp, ci, op, oracle.population_init(rp, ci, op), 100)
+        _compare_state(h, ref, m)
+
+
+@pytest.mark.parametrize("mu", [0.1, 0.4, 0.7])
+def test_lfr_40k_generations_bit_exact(mu):
+    """The benchmark graph shape (n = 40k, LFR-style) for a few generations."""
+    rp, ci, _ = synth.workload("lfr-40k", seed=1, mu=mu)
+    gp, op = _params(seed=3)
+    m = int(rp[-1] // 2)
+    with Ctx(rp, ci) as h:
+        mocd.population_init(h, gp)
+        mocd.generation(h, 2)
+        ref = oracle.run(rp, ci, op, oracle.population_init(rp, ci, op), 2)
+        _compare_state(h, ref, m)
+
+
+def test_resume_from_checkpoint_matches_uninterrupted():
+    rp, ci = GRAPHS["lfr-3k"]()
+    gp, op = _params(pop_size=40, seed=21)
+    with Ctx(rp, ci) as h:
+        mocd.population_init(h, gp)
+        mocd.generation(h, 3)
+        labels, k1, k2, gen = mocd.get_population(h)
+        mocd.generation(h, 3)
+        full = mocd.get_population(h)
+    with Ctx(rp, ci) as h2:
+        mocd.set_population(h2, gp, labels, gen)
+        assert np.array_equal(mocd.get_population(h2)[1], k1)
+        mocd.generation(h2, 3)
+        resumed = mocd.get_population(h2)
+    assert resumed[3] == full[3] == 6
+    for a, b in zip(resumed[:3], full[:3]):
+        assert np.array_equal(a, b)
+    # and the oracle agrees with the resumed state
+    ref = oracle.run(rp, ci, op, oracle.State(labels, k1, k2, gen), 3)
+    assert np.array_equal(resumed[0], ref.labels)
+
+
+def test_appendix_e_state_one_generation():
+    """Start from the App. E parents and check one generation against the oracle."""
+    d = load("appE_operator_example.txt")
+    rp, ci = graph(d)
+    P = np.stack([ints(d["parent1"]), ints(d["parent2"]), ints(d["parent3"])] * 2)
+    gp, op = _params(pop_size=6, n_parents=3, seed=2)
+    m = int(rp[-1] // 2)
+    with Ctx(rp, ci) as h:
+        mocd.set_population(h, gp, P, 0)
+        i, s = oracle.objectives(rp, ci, P)
+        ref = oracle.State(P.copy(), m - i, s, 0)
+        for _ in range(3):
+            mocd.generation(h, 1)
+            ref = oracle.run(rp, ci, op, ref, 1)
+            _compare_state(h, ref, m)
+
+
+def test_kernel_timing_reports_every_stage():
+    rp, ci = GRAPHS["planted-1k"]()
+    with Ctx(rp, ci) as h:
+        mocd.population_init(h, mocd.Params())
+        mocd.set_timing(h, True)
+        mocd.generation(h, 2)
+        t = mocd.kernel_times(h)
+        assert set(t) == set(mocd.STAGES) and all(v >= 0 for v in t.values())
+        # timing on or off does not change results
+        a = mocd.get_population(h)
+    with Ctx(rp, ci) as h:
+        mocd.population_init(h, mocd.Params())
+        mocd.generation(h, 2)
+        b = mocd.get_population(h)
+    assert np.array_equal(a[0], b[0])
+
+
+def test_invalid_params_rejected():
+    rp, ci = GRAPHS["planted-1k"]()
+    with Ctx(rp, ci) as h:
+        for bad in (dict(pop_size=0), dict(pop_size=129), dict(n_parents=17), dict(p_crossover=1.5),
+                    dict(p_mutation=-0.1), dict(init_mode=3)):
+            with pytest.raises(mocd.MocdError) as e:
+                mocd.population_init(h, mocd.Params(**bad))
+            assert e.value.status == -1
+        with pytest.raises(mocd.MocdError) as e:
+            mocd.generation(h, 1)
+        assert e.value.status == -9
