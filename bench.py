@@ -50,6 +50,8 @@ def parse_args(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--preroll-s", type=float, default=0.5,
+                    help="seconds of extra untimed generations before timing (clock settling)")
     return ap.parse_args(argv)
 
 
@@ -300,7 +302,7 @@ def run_mine(args):
     # Warm-up: W generations, then a short pre-roll so that clocks settle.
     for _ in range(args.warmup):
         mocd.generation(ctx, 1)
-    t_end = time.perf_counter() + 0.5
+    t_end = time.perf_counter() + args.preroll_s
     pre = 0
     while time.perf_counter() < t_end:
         mocd.generation(ctx, 20)

@@ -1,0 +1,75 @@
+"""Host-side logic of bench.py that needs no GPU: the max-over-ranks /
+sum-over-ranks reduction of a multi-replica run (world size 2 over gloo on
+CPU), the algorithmic byte counts and the reference (CPU oracle) arm."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    t, u = bench.reduce_step(10.0 + 3 * rank, 5.0 + rank, world)
+    bench.barrier(world)
+    out.put((rank, t, u))
+    dist.destroy_process_group()
+
+
+def test_reduce_step_two_ranks_gloo():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res == [(0, 13.0, 11.0), (1, 13.0, 11.0)]
+
+
+def test_algorithmic_bytes():
+    sys.path.insert(0, ROOT)
+    import bench
+    b = bench.algorithmic_bytes(n=1000, m=5000, np_=100, p_mut=0.2)
+    csr = 4 * 1001 + 4 * 10000
+    assert b["crossover"] == 16 * 100 * 1000
+    assert b["evaluate"] == 4 * 100 * 1000 + 4 * 100 * 10000 + 8 * 100 * 1000 + csr
+    assert b["mutation"] == 8 * 100 * 1000 + 4 * 0.2 * 100 * 10000 + csr
+
+
+def test_reference_arm_prints_one_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "planted-1k", "--steps", "3", "--warmup", "1"],
+                         capture_output=True, text=True, timeout=300, check=True)
+    lines = [l for l in out.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "planted-1k", "--steps", "2", "--warmup", "1"],
+                         capture_output=True, text=True, timeout=120, env=env)
+    assert out.returncode == 0 and out.stdout.strip() == ""
