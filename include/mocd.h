@@ -46,8 +46,12 @@ enum {
     MOCD_ERR_OUT_OF_MEMORY = -6,   /* device allocation failed */
     MOCD_ERR_BUFFER_TOO_SMALL = -7,/* caller's capacity below the result size (count set) */
     MOCD_ERR_CUDA = -8,            /* a CUDA call failed */
-    MOCD_ERR_NOT_READY = -9        /* population not initialised yet */
+    MOCD_ERR_NOT_READY = -9,       /* population not initialised yet */
+    MOCD_ERR_TOO_LARGE = -10       /* count * n exceeds MOCD_NOALLOC_MAX_CELLS */
 };
+
+/* Histogram cells (count * n) the fixed scratch of mocd_evaluate_noalloc holds. */
+#define MOCD_NOALLOC_MAX_CELLS 4194304
 
 typedef struct mocd_ctx mocd_ctx;  /* opaque; owns device memory and a stream */
 
@@ -142,6 +146,38 @@ int mocd_set_population(mocd_ctx *ctx, const mocd_params *params, const int32_t 
  */
 int mocd_evaluate(mocd_ctx *ctx, int32_t count, const int32_t *labels, int64_t *intra,
                   int64_t *sumsq);
+
+/*
+ * Objective evaluation that allocates nothing (the paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- e.g. a
+ * plug-in whose process gives all free device memory to another allocator, a
+ * component under a fixed device-memory budget, or a latency-critical loop
+ * that cannot take cudaMalloc's implicit synchronisation). It computes the
+ * same exact intra and S as mocd_evaluate, with the evaluation kernel's
+ * per-individual histogram kept in a fixed 16 MiB array compiled into the
+ * library, which every GPU that loads the library holds until exit.
+ *   row_ptr  device int32[n + 1], col_idx device int32[row_ptr[n]]: the
+ *            symmetric CSR (no self loops, no repeats; not validated here)
+ *   n        nodes, 1 <= n < 2^30
+ *   labels   device int32, node-major [n][W], W = count rounded up to a
+ *            multiple of 4, 16-byte aligned: labels[v * W + i] is individual
+ *            i's label of node v, in [0, n) (not validated here)
+ *   count    individuals, 1 <= count <= 128, with count * n <= MOCD_NOALLOC_MAX_CELLS
+ *   intra, sumsq  device int64[count], written by the call
+ *   cuda_stream   stream to issue on (NULL: the legacy default stream)
+ * The call is asynchronous on the stream and calls no cudaMalloc/cudaFree.
+ * The first call on each device looks up the scratch's device address
+ * (cudaGetSymbolAddress) on the current device; make that first call before
+ * any stream capture. All calls share the one scratch array, which keeps the
+ * previous call's contents (the call clears what it needs), so calls that
+ * overlap on the GPU -- e.g. on two streams at once -- race and give wrong
+ * results; serialise them.
+ * Errors: INVALID_ARG (null pointer, bad n or count), TOO_LARGE
+ * (count * n > MOCD_NOALLOC_MAX_CELLS), CUDA.
+ */
+int mocd_evaluate_noalloc(const int32_t *row_ptr, const int32_t *col_idx, int64_t n,
+                          const int32_t *labels, int32_t count, int64_t *intra, int64_t *sumsq,
+                          void *cuda_stream);
 
 /* Block until all work issued on the context stream is done. */
 int mocd_synchronize(mocd_ctx *ctx);

@@ -21,7 +21,7 @@ __all__ = [
     "MocdError", "Params", "Front", "library_path", "load",
     "graph_upload", "population_init", "generation", "pareto_front",
     "get_population", "set_population", "evaluate", "synchronize",
-    "set_timing", "kernel_times", "info", "destroy", "status_string",
+    "set_timing", "kernel_times", "info", "destroy", "status_string", "evaluate_noalloc",
     "STAGES",
 ]
 
@@ -101,6 +101,7 @@ def load():
         "mocd_info": (ctypes.c_int, [P, P, P, P, P]),
         "mocd_destroy": (None, [P]),
         "mocd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "mocd_evaluate_noalloc": (ctypes.c_int, [P, P, i64, P, i32, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -200,6 +201,20 @@ def evaluate(ctx, labels):
     sumsq = np.zeros(lab.shape[0], dtype=np.int64)
     _check(load().mocd_evaluate(ctx, lab.shape[0], _p(lab), _p(intra), _p(sumsq)), "mocd_evaluate")
     return intra, sumsq
+
+
+NOALLOC_MAX_CELLS = 4194304
+
+
+def evaluate_noalloc(row_ptr_dev: int, col_idx_dev: int, n: int, labels_dev: int, count: int,
+                     intra_dev: int, sumsq_dev: int, stream=None):
+    """Objective evaluation that allocates no device memory (see
+    ``mocd_evaluate_noalloc`` in include/mocd.h). Every argument except ``n``,
+    ``count`` and ``stream`` is a raw device pointer (an int); ``labels_dev``
+    is node-major ``[n][W]`` with ``W`` = ``count`` rounded up to 4. The call
+    is asynchronous on ``stream``."""
+    _check(load().mocd_evaluate_noalloc(row_ptr_dev, col_idx_dev, int(n), labels_dev, int(count), intra_dev,
+                                        sumsq_dev, _stream_handle(stream)), "mocd_evaluate_noalloc")
 
 
 def synchronize(ctx):

@@ -357,6 +357,7 @@ const char *mocd_status_string(int status)
     case MOCD_ERR_BUFFER_TOO_SMALL: return "output buffer too small";
     case MOCD_ERR_CUDA: return "CUDA error";
     case MOCD_ERR_NOT_READY: return "population not initialised";
+    case MOCD_ERR_TOO_LARGE: return "count * n exceeds the fixed scratch of the no-allocation entry point";
     default: return "unknown status";
     }
 }
