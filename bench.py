@@ -107,7 +107,8 @@ def algorithmic_bytes(n: int, m: int, np_: int, p_mut: float) -> dict:
     csr = 4 * (n + 1) + 4 * 2 * m
     return {
         "crossover": 16 * W * n,                                   # P half + Q in, next P + children out
-        "mutation": 8 * W * n + 4 * p_mut * np_ * 2 * m + csr,     # own row in, Q out, selected gathers, CSR
+        # own row in, Q out, selected pairs' neighbour labels, CSR, clearing the D_c histogram
+        "mutation": 8 * W * n + 4 * p_mut * np_ * 2 * m + csr + 4 * np_ * n,
         "evaluate": 4 * W * n + 4 * W * 2 * m + 8 * np_ * n + csr,  # own rows, neighbour rows, D_c RMW, CSR
         "select": 0,
     }

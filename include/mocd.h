@@ -186,10 +186,11 @@ int mocd_synchronize(mocd_ctx *ctx);
  * Per-kernel timing of the generation step (measurement support, not part
  * of the method): when enabled, the generation graph records CUDA events
  * between its kernels. mocd_kernel_times writes, for the most recent
- * generation, the duration in milliseconds of each stage, in this order:
- * crossover, mutation, histogram clear, evaluation, selection; returns the
- * number of stages (5) or a negative status. NOT_READY if timing is off or no
- * generation ran since it was enabled.
+ * generation, the duration in milliseconds of each kernel, in this order:
+ * crossover, mutation (which also clears the evaluation histogram),
+ * evaluation, selection; returns the number of stages (4) or a negative
+ * status. NOT_READY if timing is off or no generation ran since it was
+ * enabled.
  */
 int mocd_set_timing(mocd_ctx *ctx, int32_t enable);
 int mocd_kernel_times(mocd_ctx *ctx, float *ms, int32_t cap);

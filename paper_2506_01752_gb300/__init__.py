@@ -25,7 +25,7 @@ __all__ = [
     "STAGES",
 ]
 
-STAGES = ("crossover", "mutation", "hist_clear", "evaluate", "select")
+STAGES = ("crossover", "mutation", "evaluate", "select")
 
 OK = 0
 ERR_BUFFER_TOO_SMALL = -7

@@ -35,18 +35,22 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    os.makedirs(OUT, exist_ok=True)
-    deps_common = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "mocd.h"),
-                                                              os.path.abspath(__file__)]
+def build(force: bool = False, verbose: bool = False, extra_flags=(), src_dir: str = CSRC,
+          out_dir: str = OUT) -> str:
+    """Compile ``src_dir`` into ``out_dir/libmocd.so`` (defaults: this package)."""
+    os.makedirs(out_dir, exist_ok=True)
+    lib = os.path.join(out_dir, "libmocd.so")
+    deps_common = [os.path.join(src_dir, h) for h in HEADERS] + [os.path.join(ROOT, "include", "mocd.h"),
+                                                                 os.path.abspath(__file__)]
     nvcc = _nvcc()
+    flags = [f if f != CSRC else src_dir for f in FLAGS]
     procs, objs = [], []
     for src in SOURCES:
-        path = os.path.join(CSRC, src)
-        obj = os.path.join(OUT, src.replace(".cu", ".o"))
+        path = os.path.join(src_dir, src)
+        obj = os.path.join(out_dir, src.replace(".cu", ".o"))
         objs.append(obj)
         if force or _stale(obj, [path] + deps_common):
-            cmd = [nvcc, *ARCH, *FLAGS, *extra_flags, "-c", path, "-o", obj]
+            cmd = [nvcc, *ARCH, *flags, *extra_flags, "-c", path, "-o", obj]
             if verbose:
                 print(" ".join(cmd), file=sys.stderr)
             procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -59,11 +63,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             failed.append(src)
     if failed:
         raise RuntimeError(f"nvcc failed for {failed}")
-    if force or procs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or procs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

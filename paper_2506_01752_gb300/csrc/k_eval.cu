@@ -23,7 +23,8 @@ namespace {
 __global__ void __launch_bounds__(kBlock)
 evaluate_kernel(int n, int W, int count, const int32_t *__restrict__ row_ptr,
                 const int32_t *__restrict__ col_idx, const int32_t *__restrict__ labels,
-                uint32_t *__restrict__ hist, unsigned long long *__restrict__ acc)
+                uint32_t *__restrict__ hist, unsigned long long *__restrict__ acc,
+                const int32_t *__restrict__ order)
 {
     __shared__ unsigned long long s_intra[kMaxPop];
     __shared__ unsigned long long s_sq[kMaxPop];
@@ -44,38 +45,28 @@ evaluate_kernel(int n, int W, int count, const int32_t *__restrict__ row_ptr,
     uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
     unsigned long long q0 = 0, q1 = 0, q2 = 0, q3 = 0;
 
-    for (int v = warp; v < n; v += nwarps) {
+    for (int idx = warp; idx < n; idx += nwarps) {
+        const int v = order ? __ldg(order + idx) : idx;
         const int beg = __ldg(row_ptr + v);
         const int end = __ldg(row_ptr + v + 1);
         const int4 own = active ? L4[(size_t)v * nq + lane] : make_int4(0, 0, 0, 0);
         for (int e0 = beg; e0 < end; e0 += 32) {
             const int cnt = min(32, end - e0);
             const int my_u = lane < cnt ? __ldg(col_idx + e0 + lane) : 0;
-            int j = 0;
-            for (; j + 4 <= cnt; j += 4) {
-                const int u0 = __shfl_sync(0xffffffffu, my_u, j);
-                const int u1 = __shfl_sync(0xffffffffu, my_u, j + 1);
-                const int u2 = __shfl_sync(0xffffffffu, my_u, j + 2);
-                const int u3 = __shfl_sync(0xffffffffu, my_u, j + 3);
-                if (active) {
-                    const int4 a = L4[(size_t)u0 * nq + lane];
-                    const int4 b = L4[(size_t)u1 * nq + lane];
-                    const int4 c = L4[(size_t)u2 * nq + lane];
-                    const int4 d = L4[(size_t)u3 * nq + lane];
-                    c0 += (a.x == own.x) + (b.x == own.x) + (c.x == own.x) + (d.x == own.x);
-                    c1 += (a.y == own.y) + (b.y == own.y) + (c.y == own.y) + (d.y == own.y);
-                    c2 += (a.z == own.z) + (b.z == own.z) + (c.z == own.z) + (d.z == own.z);
-                    c3 += (a.w == own.w) + (b.w == own.w) + (c.w == own.w) + (d.w == own.w);
+            // Four independent row loads in flight per lane.
+            for (int j0 = 0; j0 < cnt; j0 += 4) {
+                int4 a[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int u = __shfl_sync(0xffffffffu, my_u, min(j0 + t, cnt - 1));
+                    a[t] = (active && j0 + t < cnt) ? L4[(size_t)u * nq + lane] : make_int4(-1, -1, -1, -1);
                 }
-            }
-            for (; j < cnt; ++j) {
-                const int u = __shfl_sync(0xffffffffu, my_u, j);
-                if (active) {
-                    const int4 a = L4[(size_t)u * nq + lane];
-                    c0 += a.x == own.x;
-                    c1 += a.y == own.y;
-                    c2 += a.z == own.z;
-                    c3 += a.w == own.w;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    c0 += a[t].x == own.x;
+                    c1 += a[t].y == own.y;
+                    c2 += a[t].z == own.z;
+                    c3 += a[t].w == own.w;
                 }
             }
         }
@@ -126,9 +117,9 @@ int grid_for_eval(int sms)
 
 cudaError_t launch_evaluate(int n, int W, int count, const int32_t *row_ptr, const int32_t *col_idx,
                             const int32_t *labels, uint32_t *hist, unsigned long long *acc,
-                            int grid, cudaStream_t s)
+                            int grid, cudaStream_t s, const int32_t *order)
 {
-    evaluate_kernel<<<grid, kBlock, 0, s>>>(n, W, count, row_ptr, col_idx, labels, hist, acc);
+    evaluate_kernel<<<grid, kBlock, 0, s>>>(n, W, count, row_ptr, col_idx, labels, hist, acc, order);
     return cudaGetLastError();
 }
 

@@ -12,6 +12,7 @@
 // then objective 2; a zero range adds nothing; fronts of one or two members
 // are all +inf. This file is built with -fmad=false; each floating-point
 // operation is one correctly rounded IEEE operation.
+#include <limits.h>
 #include <math.h>
 
 #include "mocd_internal.h"
@@ -21,101 +22,121 @@ namespace mocd {
 
 namespace {
 
-constexpr int kSelThreads = 2 * kMaxPop;  // one thread per member of R = P u Q
-constexpr int kWords = kSelThreads / 32;
+constexpr int kMaxPoints = 2 * kMaxPop;      // members of R = P u Q
+constexpr int kTpp = 4;                         // threads per point
+constexpr int kSelThreads = kMaxPoints * kTpp;  // 1024
+constexpr int kWords = kMaxPoints / 32;
+constexpr unsigned kFull = 0xffffffffu;
 
 struct SelShared {
-    long long k1[kSelThreads];
-    long long k2[kSelThreads];
-    double crowd[kSelThreads];
-    int rank[kSelThreads];
-    int order[kSelThreads];
-    int ord1[kSelThreads];
-    int ord2[kSelThreads];
-    unsigned dom[kSelThreads][kWords];  // dom[p] bit q: q dominates p
+    long long k1[kMaxPoints];
+    long long k2[kMaxPoints];
+    double crowd[kMaxPoints];
+    int rank[kMaxPoints];
+    int order[kMaxPoints];
+    int ord1[kMaxPoints];
+    int ord2[kMaxPoints];
+    unsigned dom[kMaxPoints][kWords];  // dom[p] bit q: q dominates p
     unsigned unassigned[kWords];
-    int fsize[kSelThreads + 1];
-    int foff[kSelThreads + 1];
     int keep[kMaxPop];
 };
 
-// rank[], crowd[] and order[] of the first N points of S.k1 / S.k2; thread p
-// handles point p. Ranks are 1-based.
+// Sum over the kTpp threads of one point (consecutive lanes of one warp).
+__device__ __forceinline__ int point_sum(int v)
+{
+    v += __shfl_xor_sync(kFull, v, 1);
+    v += __shfl_xor_sync(kFull, v, 2);
+    return v;
+}
+
+// rank[], crowd[] and order[] of the first N points of S.k1 / S.k2. Point p
+// is handled by threads 4p..4p+3, each taking every 4th comparison partner.
+// Ranks are 1-based.
 __device__ void rank_crowd_order(SelShared &S, int N)
 {
-    const int p = threadIdx.x;
+    const int p = threadIdx.x >> 2;
+    const int sub = threadIdx.x & 3;
+    const bool mine = p < N;
     const int nw = (N + 31) >> 5;
-    if (p < N) {
+    const int Npad = nw * 32;
+    // Padding points beyond N never dominate and never share a rank.
+    for (int q = N + (int)threadIdx.x; q < Npad; q += blockDim.x) {
+        S.k1[q] = LLONG_MAX;
+        S.k2[q] = LLONG_MAX;
+        S.rank[q] = INT_MAX;
+    }
+    __syncthreads();
+    if (mine) {
         const long long a1 = S.k1[p], a2 = S.k2[p];
-        for (int w = 0; w < nw; ++w) {
+        for (int w = sub; w < nw; w += kTpp) {
             unsigned bits = 0;
+#pragma unroll 8
             for (int b = 0; b < 32; ++b) {
-                const int q = w * 32 + b;
-                if (q < N) {
-                    const long long b1 = S.k1[q], b2 = S.k2[q];
-                    if (b1 <= a1 && b2 <= a2 && (b1 < a1 || b2 < a2)) bits |= 1u << b;
-                }
+                const long long b1 = S.k1[w * 32 + b], b2 = S.k2[w * 32 + b];
+                if (b1 <= a1 && b2 <= a2 && (b1 < a1 || b2 < a2)) bits |= 1u << b;
             }
             S.dom[p][w] = bits;
         }
     }
-    if (p < kWords) {
+    if (threadIdx.x < kWords) {
         unsigned m = 0;
-        if (p < nw) {
-            const int lo = p * 32;
-            const int cnt = min(32, N - lo);
+        if ((int)threadIdx.x < nw) {
+            const int cnt = min(32, N - (int)threadIdx.x * 32);
             m = cnt == 32 ? 0xffffffffu : ((1u << cnt) - 1u);
         }
-        S.unassigned[p] = m;
+        S.unassigned[threadIdx.x] = m;
     }
     __syncthreads();
 
-    // Peel fronts: a point joins front r when none of its dominators is
-    // still unassigned (Deb's n_p reaching zero).
+    // Peel fronts: a point joins front r when none of its dominators is still
+    // unassigned (Deb's domination count reaching zero).
     int myrank = 0;
     for (int r = 1;; ++r) {
-        bool front = false;
-        if (p < N && myrank == 0) {
-            front = true;
-            for (int w = 0; w < nw; ++w)
-                if (S.dom[p][w] & S.unassigned[w]) front = false;
-        }
+        int blocked = 0;
+        if (mine && myrank == 0)
+            for (int w = sub; w < nw; w += kTpp) blocked |= (S.dom[p][w] & S.unassigned[w]) != 0;
+        else
+            blocked = 1;
+        const bool front = point_sum(blocked) == 0;
         __syncthreads();
         if (front) {
             myrank = r;
-            atomicAnd(&S.unassigned[p >> 5], ~(1u << (p & 31)));
+            if (sub == 0) atomicAnd(&S.unassigned[p >> 5], ~(1u << (p & 31)));
         }
         if (!__syncthreads_or(front)) break;
     }
-    if (p < N) S.rank[p] = myrank;
-    for (int r = p; r <= N; r += blockDim.x) S.fsize[r] = 0;
+    if (mine && sub == 0) S.rank[p] = myrank;
     __syncthreads();
-    if (p < N) atomicAdd(&S.fsize[myrank], 1);
-    __syncthreads();
-    if (p == 0) {
-        int acc = 0;
-        for (int r = 0; r <= N; ++r) {
-            S.foff[r] = acc;
-            acc += S.fsize[r];
-        }
-    }
-    __syncthreads();
+    const int per = Npad / kTpp;  // comparison partners per thread (a multiple of 8)
 
-    int pos1 = 0, pos2 = 0;
-    if (p < N) {
+    // Front offset and size, and the position of p in its front ordered by
+    // (k1, position) and by (k2, position): counting sorts.
+    int below = 0, same = 0, pos1 = 0, pos2 = 0;
+    if (mine) {
         const long long a1 = S.k1[p], a2 = S.k2[p];
-        for (int q = 0; q < N; ++q) {
-            if (S.rank[q] != myrank) continue;
+#pragma unroll 8
+        for (int t = 0; t < per; ++t) {
+            const int q = sub + kTpp * t;
+            const int rq = S.rank[q];
             const long long b1 = S.k1[q], b2 = S.k2[q];
-            pos1 += (b1 < a1) || (b1 == a1 && q < p);
-            pos2 += (b2 < a2) || (b2 == a2 && q < p);
+            const bool sr = rq == myrank;
+            below += rq < myrank;
+            same += sr;
+            pos1 += sr && ((b1 < a1) || (b1 == a1 && q < p));
+            pos2 += sr && ((b2 < a2) || (b2 == a2 && q < p));
         }
-        S.ord1[S.foff[myrank] + pos1] = p;
-        S.ord2[S.foff[myrank] + pos2] = p;
+    }
+    below = point_sum(below);
+    same = point_sum(same);
+    pos1 = point_sum(pos1);
+    pos2 = point_sum(pos2);
+    if (mine && sub == 0) {
+        S.ord1[below + pos1] = p;
+        S.ord2[below + pos2] = p;
     }
     __syncthreads();
-    if (p < N) {
-        const int F = S.fsize[myrank], off = S.foff[myrank];
+    if (mine && sub == 0) {
+        const int F = same, off = below;
         double c;
         if (F <= 2) {
             c = INFINITY;
@@ -143,17 +164,22 @@ __device__ void rank_crowd_order(SelShared &S, int N)
         S.crowd[p] = c;
     }
     __syncthreads();
-    if (p < N) {
-        const int r = myrank;
-        const double c = S.crowd[p];
-        int pos = 0;
-        for (int q = 0; q < N; ++q) {
+    // Crowding values are non-negative or +inf (never NaN or -0), so their
+    // IEEE-754 bit patterns order exactly like the values: compare them as
+    // integers rather than on the FP64 pipe.
+    int pos = 0;
+    if (mine) {
+        const unsigned long long c = (unsigned long long)__double_as_longlong(S.crowd[p]);
+#pragma unroll 8
+        for (int t = 0; t < per; ++t) {
+            const int q = sub + kTpp * t;
             const int rq = S.rank[q];
-            const double cq = S.crowd[q];
-            pos += (rq < r) || (rq == r && (cq > c || (cq == c && q < p)));
+            const unsigned long long cq = (unsigned long long)__double_as_longlong(S.crowd[q]);
+            pos += (rq < myrank) || (rq == myrank && (cq > c || (cq == c && q < p)));
         }
-        S.order[pos] = p;
     }
+    pos = point_sum(pos);
+    if (mine && sub == 0) S.order[pos] = p;
     __syncthreads();
 }
 
@@ -161,7 +187,7 @@ __global__ void __launch_bounds__(kSelThreads)
 select_kernel(GenParams gp, PopState ps, int mode)
 {
     __shared__ SelShared S;
-    const int p = threadIdx.x;
+    const int p = threadIdx.x;  // loads, stores and the tournament: one thread per item
     const int np = gp.np;
     const long long m = gp.m;
     const uint32_t g = *ps.gen;

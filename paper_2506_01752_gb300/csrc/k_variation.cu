@@ -123,21 +123,25 @@ crossover_kernel(GenParams gp, const int32_t *buf0, const int32_t *buf1, int32_t
     extern __shared__ int smem[];
     const int W = gp.W, np = gp.np, E = gp.es;
     const int nq = W >> 2;
-    int *s_keep = smem;                  // [W]   row position of P position k
-    int *s_copy = s_keep + kMaxPop;      // [W]   row position copied, or -1
-    int *s_par = s_copy + kMaxPop;       // [np * E] row positions of parents
+    // Per-child tables, stored so that lane q reading child 4q + k hits bank q:
+    // entry (k, q) of a table lives at [k * 32 + q] (and [(j * 4 + k) * 32 + q]
+    // for parent j).
+    int *s_keep = smem;                    // row position of P position i
+    int *s_copy = s_keep + kMaxPop;        // row position copied, or -1
+    int *s_par = s_copy + kMaxPop;         // row positions of parents
     int *s_rows = s_par + kMaxPop * EMAX;  // per warp: [2W] staged row of R
 
     const uint32_t g = *gen_ptr;
     // R index r -> position in the staged row (P half at [0, W), Q at [W, 2W)).
     for (int t = threadIdx.x; t < np; t += blockDim.x) {
+        const int slot = (t & 3) * 32 + (t >> 2);
         const int r = keep[t];
-        s_keep[t] = r < np ? r : W + (r - np);
+        s_keep[slot] = r < np ? r : W + (r - np);
         const int c = copy_r[t];
-        s_copy[t] = c < 0 ? -1 : (c < np ? c : W + (c - np));
+        s_copy[slot] = c < 0 ? -1 : (c < np ? c : W + (c - np));
         for (int j = 0; j < E; ++j) {
             const int p = par_r[t * kMaxParents + j];
-            s_par[t * EMAX + j] = p < np ? p : W + (p - np);
+            s_par[(j * 4 + (t & 3)) * 32 + (t >> 2)] = p < np ? p : W + (p - np);
         }
     }
     __syncthreads();
@@ -162,7 +166,65 @@ crossover_kernel(GenParams gp, const int32_t *buf0, const int32_t *buf1, int32_t
             reinterpret_cast<int4 *>(row + W)[lane] = Q4[(size_t)v * nq + lane];
         }
         __syncwarp();
-        if (active) {
+        if (active && EMAX == 4 && E == 4) {
+            // Sort each child's four votes (5 comparators); the run pattern of
+            // the sorted values gives the maximal labels in ascending order:
+            // t = 4 (all distinct), t = 2 (two pairs) or a unique maximum. All
+            // four children are classified first so that the lane's tie word
+            // (one Philox call for its four children) is computed at most once.
+            int o[4], srt[4][4], tk[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int i = 4 * lane + k;
+                o[k] = i < np ? row[s_keep[k * 32 + lane]] : 0;
+                const int cp = i < np ? s_copy[k * 32 + lane] : 0;
+                // Children past N_p (padding of the last quad) have no parent table.
+                const bool real = i < np;
+                int s0 = row[real ? s_par[(0 * 4 + k) * 32 + lane] : 0];
+                int s1 = row[real ? s_par[(1 * 4 + k) * 32 + lane] : 0];
+                int s2 = row[real ? s_par[(2 * 4 + k) * 32 + lane] : 0];
+                int s3 = row[real ? s_par[(3 * 4 + k) * 32 + lane] : 0];
+                int lo, hi;
+                lo = min(s0, s1); hi = max(s0, s1); s0 = lo; s1 = hi;
+                lo = min(s2, s3); hi = max(s2, s3); s2 = lo; s3 = hi;
+                lo = min(s0, s2); hi = max(s0, s2); s0 = lo; s2 = hi;
+                lo = min(s1, s3); hi = max(s1, s3); s1 = lo; s3 = hi;
+                lo = min(s1, s2); hi = max(s1, s2); s1 = lo; s2 = hi;
+                const bool e01 = s0 == s1, e12 = s1 == s2, e23 = s2 == s3;
+                int t = (!e01 && !e12 && !e23) ? 4 : ((e01 && e23 && !e12) ? 2 : 1);
+                int uniq = e01 ? s0 : (e12 ? s1 : s2);
+                if (i >= np) {
+                    t = 1;
+                    uniq = 0;
+                } else if (cp >= 0) {
+                    t = 1;
+                    uniq = row[cp];
+                }
+                srt[k][0] = t == 1 ? uniq : s0;
+                srt[k][1] = s1;
+                srt[k][2] = s2;
+                srt[k][3] = s3;
+                tk[k] = t;
+            }
+            uint4 u = make_uint4(0, 0, 0, 0);
+            if (tk[0] > 1 || tk[1] > 1 || tk[2] > 1 || tk[3] > 1)
+                u = philox4x32_10(make_uint4((uint32_t)v, (uint32_t)lane, g, kStageCrossTie), gp.key0, gp.key1);
+            int r[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t w = word_of(u, k);
+                if (tk[k] == 4) {
+                    const uint32_t kk = pick_index(w, 4u);
+                    r[k] = kk == 0 ? srt[k][0] : kk == 1 ? srt[k][1] : kk == 2 ? srt[k][2] : srt[k][3];
+                } else if (tk[k] == 2) {
+                    r[k] = pick_index(w, 2u) == 0 ? srt[k][0] : srt[k][2];
+                } else {
+                    r[k] = srt[k][0];
+                }
+            }
+            D4[(size_t)v * nq + lane] = make_int4(o[0], o[1], o[2], o[3]);
+            C4[(size_t)v * nq + lane] = make_int4(r[0], r[1], r[2], r[3]);
+        } else if (active) {
             int o[4];
             int r[4];
             bool have_u = false;
@@ -170,17 +232,17 @@ crossover_kernel(GenParams gp, const int32_t *buf0, const int32_t *buf1, int32_t
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int i = 4 * lane + k;
-                o[k] = i < np ? row[s_keep[i]] : 0;
+                o[k] = i < np ? row[s_keep[k * 32 + lane]] : 0;
                 r[k] = 0;
                 if (i >= np) continue;
-                const int cp = s_copy[i];
+                const int cp = s_copy[k * 32 + lane];
                 if (cp >= 0) {
                     r[k] = row[cp];
                     continue;
                 }
                 int x[EMAX];
 #pragma unroll
-                for (int j = 0; j < EMAX; ++j) x[j] = j < E ? row[s_par[i * EMAX + j]] : 0;
+                for (int j = 0; j < EMAX; ++j) x[j] = j < E ? row[s_par[(j * 4 + k) * 32 + lane]] : 0;
                 int best;
                 const int t = mode_ties<EMAX>(x, E, best);
                 int kk = 0;
@@ -211,29 +273,25 @@ crossover_kernel(GenParams gp, const int32_t *buf0, const int32_t *buf1, int32_t
 // count table in shared memory.
 // ---------------------------------------------------------------------------
 
-// k-th smallest label held by the lanes of `cand` (distinct labels), by
-// binary radix selection over the label bits.
-__device__ __forceinline__ int select_kth_lane(unsigned cand, int x, unsigned k, int bits)
+// The k-th smallest of the distinct labels held by the lanes of `cand`: the
+// minimum is removed k times (labels are non-negative).
+__device__ __forceinline__ int select_kth_lane(unsigned cand, int x, unsigned k)
 {
     unsigned act = cand;
-    for (int b = bits - 1; b >= 0; --b) {
-        const unsigned zero = __ballot_sync(kFull, ((x >> b) & 1) == 0) & act;
-        const unsigned c = __popc(zero);
-        if (k < c) {
-            act = zero;
-        } else {
-            k -= c;
-            act &= ~zero;
-        }
+    const int lane = threadIdx.x & 31;
+    for (unsigned s = 0; s < k; ++s) {
+        const unsigned mn = __reduce_min_sync(kFull, ((act >> lane) & 1u) ? (unsigned)x : 0xffffffffu);
+        act &= ~__ballot_sync(kFull, ((act >> lane) & 1u) && (unsigned)x == mn);
     }
-    return __ffs(act) - 1;
+    const unsigned mn = __reduce_min_sync(kFull, ((act >> lane) & 1u) ? (unsigned)x : 0xffffffffu);
+    return __ffs(__ballot_sync(kFull, ((act >> lane) & 1u) && (unsigned)x == mn)) - 1;
 }
 
-__device__ __forceinline__ uint32_t tie_word(const GenParams &gp, int v, int i, uint32_t g)
+// MTIE words of the lane's four children at node v (computed by every lane
+// together, the first time a tie occurs at v).
+__device__ __forceinline__ uint4 tie_words(const GenParams &gp, int v, int lane, uint32_t g)
 {
-    const uint4 r = philox4x32_10(make_uint4((uint32_t)v, (uint32_t)(i >> 2), g, kStageMutTie),
-                                  gp.key0, gp.key1);
-    return word_of(r, i & 3);
+    return philox4x32_10(make_uint4((uint32_t)v, (uint32_t)lane, g, kStageMutTie), gp.key0, gp.key1);
 }
 
 __device__ __forceinline__ uint32_t hash_slot(int x, int hbits)
@@ -241,10 +299,85 @@ __device__ __forceinline__ uint32_t hash_slot(int x, int hbits)
     return ((uint32_t)x * 2654435761u) >> (32 - hbits);
 }
 
-__global__ void __launch_bounds__(kBlock)
+constexpr int kTileStride = 33;  // padded row of the per-warp label tile
+constexpr int kTileRows = 64;    // neighbours whose labels the tile keeps
+constexpr int kMutBlock = 128;   // mutation threads per block (shared memory bound)
+
+// Exact neighbour-majority of one (node, child) pair by the whole warp
+// (lane = neighbour); used for the pairs without a strict majority.
+__device__ __forceinline__ int warp_mode(const GenParams &gp, const int32_t *__restrict__ child,
+                                         const int32_t *__restrict__ col_idx, int beg, int deg,
+                                         const int *tile_col, int i, int *hkey, int *hcnt, int hbits,
+                                         uint32_t tie_u)
+{
+    const int lane = threadIdx.x & 31;
+    const int W = gp.W;
+    if (deg <= 32) {
+        // tile_col[j * kTileStride] holds this pair's label of neighbour j
+        // (for the first kTileRows neighbours).
+        const unsigned lt = (1u << lane) - 1u;
+        const int x = lane < deg ? tile_col[lane * kTileStride] : (int)(0x80000000u | lane);
+        const unsigned peers = __match_any_sync(kFull, x);
+        const unsigned cnt = lane < deg ? __popc(peers) : 0u;
+        const unsigned mx = __reduce_max_sync(kFull, cnt);
+        const unsigned cand = __ballot_sync(kFull, lane < deg && cnt == mx && (peers & lt) == 0);
+        const int t = __popc(cand);
+        const int src = t == 1 ? __ffs(cand) - 1 : select_kth_lane(cand, x, pick_index(tie_u, (uint32_t)t));
+        return __shfl_sync(kFull, x, src);
+    }
+    const int HS = 1 << hbits;
+    const int per_lane = HS >> 5;
+    for (int e = lane; e < HS; e += 32) {
+        hkey[e] = -1;
+        hcnt[e] = 0;
+    }
+    __syncwarp();
+    for (int e0 = 0; e0 < deg; e0 += 32) {
+        if (e0 + lane < deg) {
+            const int x = deg <= kTileRows ? tile_col[(e0 + lane) * kTileStride]
+                                           : child[(size_t)__ldg(col_idx + beg + e0 + lane) * W + i];
+            uint32_t h = hash_slot(x, hbits);
+            // The table holds at most deg < HS / 2 distinct labels, so an empty
+            // or matching slot is always found.
+            for (int probe = 0; probe < HS; ++probe) {
+                const int prev = atomicCAS(hkey + h, -1, x);
+                if (prev == -1 || prev == x) {
+                    atomicAdd(hcnt + h, 1);
+                    break;
+                }
+                h = (h + 1) & (uint32_t)(HS - 1);
+            }
+        }
+    }
+    __syncwarp();
+    unsigned mx_l = 0;
+    for (int s = 0; s < per_lane; ++s) mx_l = max(mx_l, (unsigned)hcnt[lane + 32 * s]);
+    const unsigned mx = __reduce_max_sync(kFull, mx_l);
+    unsigned act = 0;
+    for (int s = 0; s < per_lane; ++s)
+        if ((unsigned)hcnt[lane + 32 * s] == mx) act |= 1u << s;
+    const unsigned t = __reduce_add_sync(kFull, (unsigned)__popc(act));
+    const unsigned kk = t > 1 ? pick_index(tie_u, t) : 0u;
+    // Remove the smallest tied label kk times; the next smallest wins.
+    unsigned mn = 0;
+    for (unsigned s = 0; s <= kk; ++s) {
+        unsigned my = 0xffffffffu;
+        for (int e = 0; e < per_lane; ++e)
+            if ((act >> e) & 1u) my = min(my, (unsigned)hkey[lane + 32 * e]);
+        mn = __reduce_min_sync(kFull, my);
+        if (s < kk)
+            for (int e = 0; e < per_lane; ++e)
+                if (((act >> e) & 1u) && (unsigned)hkey[lane + 32 * e] == mn) act &= ~(1u << e);
+    }
+    __syncwarp();
+    return (int)mn;
+}
+
+__global__ void __launch_bounds__(kMutBlock, 8)
 mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
-                const int32_t *__restrict__ child, int32_t *__restrict__ q,
-                const uint32_t *__restrict__ gen_ptr)
+                const int32_t *__restrict__ order, const int32_t *__restrict__ child, int32_t *__restrict__ q,
+                const uint32_t *__restrict__ gen_ptr, uint32_t *__restrict__ hist,
+                unsigned long long *__restrict__ acc)
 {
     extern __shared__ int smem[];
     const int W = gp.W, np = gp.np;
@@ -254,7 +387,10 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
     const int wib = threadIdx.x >> 5;
     const int HS = gp.hash_size;
     const int hbits = HS > 0 ? __ffs(HS) - 1 : 0;
-    int *hkey = smem + wib * 2 * HS;
+    int *s_list = smem + wib * (2 * kMaxPop + kTileRows * kTileStride + 2 * HS);  // selected children
+    int *s_res = s_list + kMaxPop;              // by child index: v's own label, then the result
+    int *tile = s_res + kMaxPop;                // [kTileRows][kTileStride]: label of neighbour j, pair lane
+    int *hkey = tile + kTileRows * kTileStride;
     int *hcnt = hkey + HS;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -262,125 +398,143 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
     const int4 *__restrict__ C4 = reinterpret_cast<const int4 *>(child);
     int4 *__restrict__ Q4 = reinterpret_cast<int4 *>(q);
 
-    for (int v = warp; v < gp.n; v += nwarps) {
+    // The evaluation that follows accumulates into hist and acc: clear them
+    // here, overlapped with this compute-bound kernel.
+    {
+        const size_t words = (size_t)np * (size_t)gp.n;
+        uint4 *h4 = reinterpret_cast<uint4 *>(hist);
+        const size_t n4 = words >> 2;
+        for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n4; t += (size_t)gridDim.x * blockDim.x)
+            h4[t] = make_uint4(0, 0, 0, 0);
+        for (size_t t = (n4 << 2) + blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < words;
+             t += (size_t)gridDim.x * blockDim.x)
+            hist[t] = 0;
+        if (blockIdx.x == 0)
+            for (int t = threadIdx.x; t < 2 * kMaxPop; t += blockDim.x) acc[t] = 0;
+    }
+
+    // Nodes in degree-descending order: every warp starts with one of the
+    // costliest nodes, which balances the grid-stride loop.
+    for (int idx = warp; idx < gp.n; idx += nwarps) {
+        const int v = __ldg(order + idx);
         const int beg = __ldg(row_ptr + v);
         const int end = __ldg(row_ptr + v + 1);
         const int deg = end - beg;
         int4 out = active ? C4[(size_t)v * nq + lane] : make_int4(0, 0, 0, 0);
-        bool s0 = false, s1 = false, s2 = false, s3 = false;
+        unsigned sel = 0;  // bit k: child 4 * lane + k mutates
         if (active && deg > 0) {
             const uint4 r = philox4x32_10(make_uint4((uint32_t)v, (uint32_t)lane, g, kStageMutCoin),
                                           gp.key0, gp.key1);
             const int i0 = 4 * lane;
-            s0 = i0 + 0 < np && (unsigned long long)r.x < gp.thr_m;
-            s1 = i0 + 1 < np && (unsigned long long)r.y < gp.thr_m;
-            s2 = i0 + 2 < np && (unsigned long long)r.z < gp.thr_m;
-            s3 = i0 + 3 < np && (unsigned long long)r.w < gp.thr_m;
+            sel = ((i0 + 0 < np && (unsigned long long)r.x < gp.thr_m) ? 1u : 0u) |
+                  ((i0 + 1 < np && (unsigned long long)r.y < gp.thr_m) ? 2u : 0u) |
+                  ((i0 + 2 < np && (unsigned long long)r.z < gp.thr_m) ? 4u : 0u) |
+                  ((i0 + 3 < np && (unsigned long long)r.w < gp.thr_m) ? 8u : 0u);
         }
-        const unsigned b[4] = {__ballot_sync(kFull, s0), __ballot_sync(kFull, s1),
-                               __ballot_sync(kFull, s2), __ballot_sync(kFull, s3)};
-        if ((b[0] | b[1] | b[2] | b[3]) != 0) {
-            if (deg <= 32) {
-                const int my_u = lane < deg ? __ldg(col_idx + beg + lane) : 0;
-                const unsigned lt = (1u << lane) - 1u;
+        // Compact the selected children of v into s_list (warp prefix sum).
+        const int mine = __popc(sel);
+        int incl = mine;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    unsigned msk = b[k];
-                    while (msk) {
-                        const int ql = __ffs(msk) - 1;
-                        msk &= msk - 1;
-                        const int i = 4 * ql + k;
-                        const int x = lane < deg ? child[(size_t)my_u * W + i] : (int)(0x80000000u | lane);
-                        const unsigned peers = __match_any_sync(kFull, x);
-                        const unsigned cnt = lane < deg ? __popc(peers) : 0u;
-                        const unsigned mx = __reduce_max_sync(kFull, cnt);
-                        const unsigned cand = __ballot_sync(kFull, lane < deg && cnt == mx && (peers & lt) == 0);
-                        const int t = __popc(cand);
-                        int src;
-                        if (t == 1) {
-                            src = __ffs(cand) - 1;
-                        } else {
-                            const uint32_t u = tie_word(gp, v, i, g);
-                            src = select_kth_lane(cand, x, pick_index(u, (uint32_t)t), gp.label_bits);
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, d);
+            if (lane >= d) incl += y;
+        }
+        const int nsel = __shfl_sync(kFull, incl, 31);
+        if (nsel > 0) {
+            int at = incl - mine;
+            for (int k = 0; k < 4; ++k)
+                if ((sel >> k) & 1u) s_list[at++] = 4 * lane + k;
+            if (active) reinterpret_cast<int4 *>(s_res)[lane] = out;
+            __syncwarp();
+            const int my_u0 = lane < deg ? __ldg(col_idx + beg + lane) : 0;
+            bool have_tw = false;
+            uint4 tw = make_uint4(0, 0, 0, 0);
+            for (int base = 0; base < nsel; base += 32) {
+                // Lane = pair. A label held by more than deg / 2 neighbours is the
+                // unique most frequent one: find the Boyer-Moore candidate, then
+                // count it.
+                const bool has = base + lane < nsel;
+                const int i = has ? s_list[base + lane] : 0;
+                // Pass 1: Boyer-Moore candidate and the count of the node's own
+                // label (usually the strict majority once the population has
+                // converged), eight independent loads in flight; the first 32
+                // neighbours' labels are kept in the tile.
+                const int own = has ? s_res[i] : 0;
+                int cand = 0, run = 0, hits = 0, own_hits = 0;
+                for (int e0 = 0; e0 < deg; e0 += 32) {
+                    const int my_u = e0 == 0 ? my_u0 : (e0 + lane < deg ? __ldg(col_idx + beg + e0 + lane) : 0);
+                    const int cnt = min(32, deg - e0);
+                    for (int j0 = 0; j0 < cnt; j0 += 8) {
+                        int xs[8];
+#pragma unroll
+                        for (int t = 0; t < 8; ++t) {
+                            const int u = __shfl_sync(kFull, my_u, min(j0 + t, cnt - 1));
+                            xs[t] = (has && j0 + t < cnt) ? child[(size_t)u * W + i] : 0;
                         }
-                        const int lab = __shfl_sync(kFull, x, src);
-                        if (lane == ql) {
-                            if (k == 0) out.x = lab;
-                            else if (k == 1) out.y = lab;
-                            else if (k == 2) out.z = lab;
-                            else out.w = lab;
-                        }
-                    }
-                }
-            } else {
-                const int per_lane = HS >> 5;  // table entries owned by each lane when scanning
-#pragma unroll 1
-                for (int k = 0; k < 4; ++k) {
-                    unsigned msk = b[k];
-                    while (msk) {
-                        const int ql = __ffs(msk) - 1;
-                        msk &= msk - 1;
-                        const int i = 4 * ql + k;
-                        for (int e = lane; e < HS; e += 32) {
-                            hkey[e] = -1;
-                            hcnt[e] = 0;
-                        }
-                        __syncwarp();
-                        for (int e0 = beg; e0 < end; e0 += 32) {
-                            if (e0 + lane < end) {
-                                const int x = child[(size_t)__ldg(col_idx + e0 + lane) * W + i];
-                                uint32_t h = hash_slot(x, hbits);
-                                // The table holds at most deg < HS / 2 distinct labels,
-                                // so an empty or matching slot is always found.
-                                for (int probe = 0; probe < HS; ++probe) {
-                                    const int prev = atomicCAS(hkey + h, -1, x);
-                                    if (prev == -1 || prev == x) {
-                                        atomicAdd(hcnt + h, 1);
-                                        break;
-                                    }
-                                    h = (h + 1) & (uint32_t)(HS - 1);
+#pragma unroll
+                        for (int t = 0; t < 8; ++t) {
+                            if (has && j0 + t < cnt) {
+                                const int x = xs[t];
+                                own_hits += x == own;
+                                if (run == 0) {
+                                    cand = x;
+                                    run = 1;
+                                } else {
+                                    run += x == cand ? 1 : -1;
                                 }
+                                if (e0 + j0 + t < kTileRows) tile[(e0 + j0 + t) * kTileStride + lane] = x;
                             }
                         }
-                        __syncwarp();
-                        unsigned mx_l = 0;
-                        for (int s = 0; s < per_lane; ++s) {
-                            const unsigned c = (unsigned)hcnt[lane + 32 * s];
-                            mx_l = c > mx_l ? c : mx_l;
-                        }
-                        const unsigned mx = __reduce_max_sync(kFull, mx_l);
-                        unsigned act = 0;
-                        for (int s = 0; s < per_lane; ++s)
-                            if ((unsigned)hcnt[lane + 32 * s] == mx) act |= 1u << s;
-                        const unsigned t = __reduce_add_sync(kFull, (unsigned)__popc(act));
-                        unsigned kk = 0;
-                        if (t > 1) kk = pick_index(tie_word(gp, v, i, g), t);
-                        for (int bit = gp.label_bits - 1; bit >= 0 && t > 1; --bit) {
-                            unsigned zero = 0;
-                            for (int s = 0; s < per_lane; ++s)
-                                if (((act >> s) & 1u) && ((hkey[lane + 32 * s] >> bit) & 1) == 0) zero |= 1u << s;
-                            const unsigned c = __reduce_add_sync(kFull, (unsigned)__popc(zero));
-                            if (kk < c) {
-                                act = zero;
-                            } else {
-                                kk -= c;
-                                act &= ~zero;
-                            }
-                        }
-                        const unsigned holder = __ballot_sync(kFull, act != 0);
-                        const int src = __ffs(holder) - 1;
-                        const int mine = act ? hkey[lane + 32 * (__ffs(act) - 1)] : 0;
-                        const int lab = __shfl_sync(kFull, mine, src);
-                        if (lane == ql) {
-                            if (k == 0) out.x = lab;
-                            else if (k == 1) out.y = lab;
-                            else if (k == 2) out.z = lab;
-                            else out.w = lab;
-                        }
-                        __syncwarp();
                     }
                 }
+                // Pass 2 (only when the own label is not a strict majority and the
+                // candidate differs from it): count the candidate.
+                bool own_wins = has && 2 * own_hits > deg;
+                if (own_wins) cand = own;
+                const bool need2 = has && !own_wins && cand != own;
+                if (need2 && deg <= kTileRows)
+                    for (int j = 0; j < deg; ++j) hits += tile[j * kTileStride + lane] == cand;
+                if (deg > kTileRows && __any_sync(kFull, need2)) {
+                    for (int e0 = 0; e0 < deg; e0 += 32) {
+                        const int my_u = e0 == 0 ? my_u0 : (e0 + lane < deg ? __ldg(col_idx + beg + e0 + lane) : 0);
+                        const int cnt = min(32, deg - e0);
+                        for (int j0 = 0; j0 < cnt; j0 += 8) {
+                            int xs[8];
+#pragma unroll
+                            for (int t = 0; t < 8; ++t) {
+                                const int u = __shfl_sync(kFull, my_u, min(j0 + t, cnt - 1));
+                                xs[t] = (need2 && j0 + t < cnt) ? child[(size_t)u * W + i] : 0;
+                            }
+#pragma unroll
+                            for (int t = 0; t < 8; ++t) hits += (need2 && j0 + t < cnt && xs[t] == cand) ? 1 : 0;
+                        }
+                    }
+                }
+                if (own_wins) hits = own_hits;
+                __syncwarp();
+                const bool done = has && 2 * hits > deg;
+                if (done) s_res[i] = cand;
+                unsigned rest = __ballot_sync(kFull, has && !done);
+                while (rest) {
+                    const int l = __ffs(rest) - 1;
+                    rest &= rest - 1;
+                    const int ic = __shfl_sync(kFull, i, l);
+                    if (!have_tw) {
+                        tw = tie_words(gp, v, lane, g);
+                        have_tw = true;
+                    }
+                    const uint32_t u = __shfl_sync(kFull, word_of(tw, ic & 3), ic >> 2);
+                    const int lab = warp_mode(gp, child, col_idx, beg, deg, tile + l, ic, hkey, hcnt, hbits, u);
+                    if (lane == 0) s_res[ic] = lab;
+                }
+                __syncwarp();
             }
+            __syncwarp();
+            if (sel & 1u) out.x = s_res[4 * lane + 0];
+            if (sel & 2u) out.y = s_res[4 * lane + 1];
+            if (sel & 4u) out.z = s_res[4 * lane + 2];
+            if (sel & 8u) out.w = s_res[4 * lane + 3];
+            __syncwarp();
         }
         if (active) Q4[(size_t)v * nq + lane] = out;
     }
@@ -430,23 +584,28 @@ cudaError_t launch_crossover(const GenParams &gp, const PopState &ps, int grid, 
     return cudaGetLastError();
 }
 
+int mutation_smem(int hash_size)
+{
+    return (kMutBlock / 32) * (2 * kMaxPop + kTileRows * kTileStride + 2 * hash_size) * (int)sizeof(int);
+}
+
 int grid_for_mutation(int sms, int hash_size, int *smem_bytes)
 {
-    const int smem = (kBlock / 32) * 2 * hash_size * (int)sizeof(int);
+    const int smem = mutation_smem(hash_size);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(mutation_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mutation_kernel, kBlock, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mutation_kernel, kMutBlock, smem);
     if (per_sm < 1) per_sm = 1;
     *smem_bytes = smem;
     return sms * per_sm;
 }
 
 cudaError_t launch_mutation(const GenParams &gp, const PopState &ps, const int32_t *row_ptr,
-                            const int32_t *col_idx, int grid, cudaStream_t s)
+                            const int32_t *col_idx, const int32_t *order, int grid, cudaStream_t s)
 {
-    const int smem = (kBlock / 32) * 2 * gp.hash_size * (int)sizeof(int);
-    mutation_kernel<<<grid, kBlock, smem, s>>>(gp, row_ptr, col_idx, ps.c, ps.q, ps.gen);
+    mutation_kernel<<<grid, kMutBlock, mutation_smem(gp.hash_size), s>>>(gp, row_ptr, col_idx, order, ps.c, ps.q,
+                                                                       ps.gen, ps.hist, ps.acc);
     return cudaGetLastError();
 }
 

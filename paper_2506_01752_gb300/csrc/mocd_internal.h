@@ -9,6 +9,8 @@
 //   hist     uint32 [Np][n] per-individual community degree totals D_c
 //                            (scratch, cleared before every evaluation)
 //   CSR      int32 row_ptr[n + 1], int32 col_idx[2m] (symmetric)
+//   order    int32[n] nodes by degree, descending (work order of the
+//            degree-proportional kernels; results do not depend on it)
 #pragma once
 
 #include <cuda_runtime.h>
@@ -62,11 +64,13 @@ struct GenParams {
 // Launch wrappers (stream-ordered, return cudaGetLastError()).
 cudaError_t launch_init_population(const GenParams &gp, int32_t *dst, cudaStream_t s);
 cudaError_t launch_crossover(const GenParams &gp, const PopState &ps, int grid, cudaStream_t s);
+// order: the nodes in the sequence the grid-stride loop visits them
+// (degree descending), or NULL for 0..n-1 (evaluation only).
 cudaError_t launch_mutation(const GenParams &gp, const PopState &ps, const int32_t *row_ptr,
-                            const int32_t *col_idx, int grid, cudaStream_t s);
+                            const int32_t *col_idx, const int32_t *order, int grid, cudaStream_t s);
 cudaError_t launch_evaluate(int n, int W, int count, const int32_t *row_ptr, const int32_t *col_idx,
                             const int32_t *labels, uint32_t *hist, unsigned long long *acc,
-                            int grid, cudaStream_t s);
+                            int grid, cudaStream_t s, const int32_t *order = nullptr);
 // mode 0: keys of a fresh P from acc, keep = identity; mode 1: R = P u Q,
 // environmental selection. Both then rank P and draw the next tournament.
 cudaError_t launch_select(const GenParams &gp, const PopState &ps, int mode, cudaStream_t s);

@@ -20,7 +20,7 @@ using namespace mocd;
 
 namespace {
 
-constexpr int kStages = 5;
+constexpr int kStages = 4;
 
 }  // namespace
 
@@ -34,6 +34,7 @@ struct mocd_ctx {
     int dmax = 0;
     int32_t *d_row_ptr = nullptr;
     int32_t *d_col_idx = nullptr;
+    int32_t *d_order = nullptr;   // nodes by degree, descending
 
     // Population.
     bool ready = false;
@@ -241,7 +242,8 @@ cudaError_t mark(mocd_ctx *c, int k)
     return cudaEventRecordWithFlags(c->ev[k], c->stream, cudaEventRecordExternal);
 }
 
-// One generation of Alg. 1 on the context stream.
+// One generation of Alg. 1 on the context stream. The mutation kernel also
+// clears the histogram and accumulators that the evaluation then fills.
 int issue_generation(mocd_ctx *c, bool events)
 {
     const GenParams &gp = c->gp;
@@ -249,16 +251,13 @@ int issue_generation(mocd_ctx *c, bool events)
     if (events) CK(mark(c, 0));
     CK(launch_crossover(gp, ps, c->grid_cross, c->stream));
     if (events) CK(mark(c, 1));
-    CK(launch_mutation(gp, ps, c->d_row_ptr, c->d_col_idx, c->grid_mut, c->stream));
+    CK(launch_mutation(gp, ps, c->d_row_ptr, c->d_col_idx, c->d_order, c->grid_mut, c->stream));
     if (events) CK(mark(c, 2));
-    int rc = clear_eval_state(c, ps.hist, (size_t)gp.np * (size_t)gp.n, ps.acc);
-    if (rc) return rc;
-    if (events) CK(mark(c, 3));
     CK(launch_evaluate(gp.n, gp.W, gp.np, c->d_row_ptr, c->d_col_idx, ps.q, ps.hist, ps.acc,
-                       c->grid_eval, c->stream));
-    if (events) CK(mark(c, 4));
+                       c->grid_eval, c->stream, c->d_order));
+    if (events) CK(mark(c, 3));
     CK(launch_select(gp, ps, 1, c->stream));
-    if (events) CK(mark(c, 5));
+    if (events) CK(mark(c, 4));
     return MOCD_OK;
 }
 
@@ -425,6 +424,19 @@ int mocd_graph_upload(mocd_ctx **out, int64_t n, const int64_t *row_ptr, const i
     e = cudaMalloc(&p, sizeof(int32_t) * nnz);
     if (e != cudaSuccess) return fail(cuda_status(e));
     c->d_col_idx = static_cast<int32_t *>(p);
+    // Work order of the degree-proportional kernels: degree descending (ties
+    // by node id), so that the costliest nodes are spread over all warps.
+    std::vector<int32_t> order(n);
+    for (int64_t v = 0; v < n; ++v) order[v] = (int32_t)v;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return row_ptr[a + 1] - row_ptr[a] > row_ptr[b + 1] - row_ptr[b];
+    });
+    e = cudaMalloc(&p, sizeof(int32_t) * n);
+    if (e != cudaSuccess) return fail(cuda_status(e));
+    c->d_order = static_cast<int32_t *>(p);
+    if (cudaMemcpyAsync(c->d_order, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream) !=
+        cudaSuccess)
+        return fail(MOCD_ERR_CUDA);
     if (cudaMemcpyAsync(c->d_row_ptr, rp32.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice,
                         c->stream) != cudaSuccess ||
         cudaMemcpyAsync(c->d_col_idx, adj.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice,
@@ -610,6 +622,7 @@ void mocd_destroy(mocd_ctx *c)
     free_population(c);
     cudaFree(c->d_row_ptr);
     cudaFree(c->d_col_idx);
+    cudaFree(c->d_order);
     cudaFree(c->d_im);
     cudaFree(c->d_nm);
     cudaFree(c->d_eval_acc);

@@ -53,7 +53,7 @@ def test_algorithmic_bytes():
     csr = 4 * 1001 + 4 * 10000
     assert b["crossover"] == 16 * 100 * 1000
     assert b["evaluate"] == 4 * 100 * 1000 + 4 * 100 * 10000 + 8 * 100 * 1000 + csr
-    assert b["mutation"] == 8 * 100 * 1000 + 4 * 0.2 * 100 * 10000 + csr
+    assert b["mutation"] == 8 * 100 * 1000 + 4 * 0.2 * 100 * 10000 + csr + 4 * 100 * 1000
 
 
 def test_reference_arm_prints_one_line():
