@@ -22,164 +22,232 @@ namespace mocd {
 
 namespace {
 
-constexpr int kMaxPoints = 2 * kMaxPop;      // members of R = P u Q
-constexpr int kTpp = 4;                         // threads per point
-constexpr int kSelThreads = kMaxPoints * kTpp;  // 1024
-constexpr int kWords = kMaxPoints / 32;
+constexpr int kMaxPoints = 2 * kMaxPop;   // members of R = P u Q
+constexpr int kSelThreads = kMaxPoints;     // one thread per point
+constexpr int kSelWarps = kSelThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned long long kInf64 = 0xffffffffffffffffull;
+
+// Sort key: the pair (a, b) in lexicographic order of unsigned words. Every
+// key a sort sees is distinct (the point index is packed into b).
+struct Key {
+    unsigned long long a, b;
+};
+
+__device__ __forceinline__ bool key_less(const Key &x, const Key &y)
+{
+    return x.a < y.a || (x.a == y.a && x.b < y.b);
+}
 
 struct SelShared {
     long long k1[kMaxPoints];
     long long k2[kMaxPoints];
-    double crowd[kMaxPoints];
-    int rank[kMaxPoints];
-    int order[kMaxPoints];
-    int ord1[kMaxPoints];
-    int ord2[kMaxPoints];
-    unsigned dom[kMaxPoints][kWords];  // dom[p] bit q: q dominates p
-    unsigned unassigned[kWords];
+    int rank[kMaxPoints];        // by point
+    double crowd[kMaxPoints];    // by point
+    int order[kMaxPoints];       // (rank, crowding desc, index) order
+    // scratch by sorted position
+    unsigned long long sa[kMaxPoints], sb[kMaxPoints];
+    int ia[kMaxPoints], ib[kMaxPoints];
+    unsigned long long wscan[kSelWarps];
+    int fsize[kMaxPoints + 1];
     int keep[kMaxPop];
 };
 
-// Sum over the kTpp threads of one point (consecutive lanes of one warp).
-__device__ __forceinline__ int point_sum(int v)
+// Bitonic sort of one key per thread across the block (kSelThreads keys),
+// ascending; the compare-exchange is branch-free.
+__device__ __forceinline__ Key block_sort(SelShared &S, Key key)
 {
-    v += __shfl_xor_sync(kFull, v, 1);
-    v += __shfl_xor_sync(kFull, v, 2);
-    return v;
+    const int t = threadIdx.x;
+#pragma unroll 1
+    for (int k = 2; k <= kSelThreads; k <<= 1) {
+#pragma unroll 1
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            Key other;
+            if (j >= 32) {
+                S.sa[t] = key.a;
+                S.sb[t] = key.b;
+                __syncthreads();
+                other.a = S.sa[t ^ j];
+                other.b = S.sb[t ^ j];
+                __syncthreads();
+            } else {
+                other.a = __shfl_xor_sync(kFull, key.a, j);
+                other.b = __shfl_xor_sync(kFull, key.b, j);
+            }
+            // Keep the smaller key where (t is the lower index) == (ascending run).
+            const bool want_min = ((t & j) == 0) == ((t & k) == 0);
+            const bool take = key_less(other, key) == want_min;
+            key.a = take ? other.a : key.a;
+            key.b = take ? other.b : key.b;
+        }
+    }
+    return key;
 }
 
-// rank[], crowd[] and order[] of the first N points of S.k1 / S.k2. Point p
-// is handled by threads 4p..4p+3, each taking every 4th comparison partner.
-// Ranks are 1-based.
+// Inclusive block-wide scans over thread order (min of u64, max of int).
+__device__ unsigned long long block_min_scan(SelShared &S, unsigned long long v)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, v, d);
+        if (lane >= d) v = min(v, y);
+    }
+    if (lane == 31) S.wscan[w] = v;
+    __syncthreads();
+    unsigned long long pre = kInf64;
+    for (int q = 0; q < w; ++q) pre = min(pre, S.wscan[q]);
+    __syncthreads();
+    return min(v, pre);
+}
+
+__device__ int block_max_scan(SelShared &S, int v)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(kFull, v, d);
+        if (lane >= d) v = max(v, y);
+    }
+    if (lane == 31) S.wscan[w] = (unsigned long long)(unsigned)v;
+    __syncthreads();
+    int pre = 0;
+    for (int q = 0; q < w; ++q) pre = max(pre, (int)(unsigned)S.wscan[q]);
+    __syncthreads();
+    return max(v, pre);
+}
+
+// rank[], crowd[] and order[] of the first N points of S.k1 / S.k2 (N <= 256),
+// all indexed by point; ranks are 1-based. Same definitions as the textbook
+// O(N^2) procedure, computed with three block sorts and a few scans.
 __device__ void rank_crowd_order(SelShared &S, int N)
 {
-    const int p = threadIdx.x >> 2;
-    const int sub = threadIdx.x & 3;
-    const bool mine = p < N;
-    const int nw = (N + 31) >> 5;
-    const int Npad = nw * 32;
-    // Padding points beyond N never dominate and never share a rank.
-    for (int q = N + (int)threadIdx.x; q < Npad; q += blockDim.x) {
-        S.k1[q] = LLONG_MAX;
-        S.k2[q] = LLONG_MAX;
-        S.rank[q] = INT_MAX;
-    }
-    __syncthreads();
-    if (mine) {
-        const long long a1 = S.k1[p], a2 = S.k2[p];
-        for (int w = sub; w < nw; w += kTpp) {
-            unsigned bits = 0;
-#pragma unroll 8
-            for (int b = 0; b < 32; ++b) {
-                const long long b1 = S.k1[w * 32 + b], b2 = S.k2[w * 32 + b];
-                if (b1 <= a1 && b2 <= a2 && (b1 < a1 || b2 < a2)) bits |= 1u << b;
-            }
-            S.dom[p][w] = bits;
-        }
-    }
-    if (threadIdx.x < kWords) {
-        unsigned m = 0;
-        if ((int)threadIdx.x < nw) {
-            const int cnt = min(32, N - (int)threadIdx.x * 32);
-            m = cnt == 32 ? 0xffffffffu : ((1u << cnt) - 1u);
-        }
-        S.unassigned[threadIdx.x] = m;
-    }
-    __syncthreads();
+    const int t = threadIdx.x;
+    const bool valid = t < N;
 
-    // Peel fronts: a point joins front r when none of its dominators is still
-    // unassigned (Deb's domination count reaching zero).
+    // (1) Sort by (k1, k2, index); invalid points go last. k1 < 2^31, so
+    // (k1 : hi32(k2), lo32(k2) : index) orders like the triple.
+    Key k;
+    {
+        const unsigned long long k1 = valid ? (unsigned long long)S.k1[t] : 0xffffffffull;
+        const unsigned long long k2 = valid ? (unsigned long long)S.k2[t] : kInf64;
+        k.a = (k1 << 32) | (k2 >> 32);
+        k.b = (k2 << 32) | (unsigned long long)t;
+    }
+    k = block_sort(S, k);
+    // Thread t now holds sorted position t.
+    const int id = (int)(k.b & 0xffffffffull);
+    const bool real = id < N;
+    const unsigned long long my1 = k.a >> 32;
+    const unsigned long long my2 = ((k.a & 0xffffffffull) << 32) | (k.b >> 32);
+    S.sa[t] = my1;
+    S.sb[t] = my2;
+    __syncthreads();
+    // Start of t's group of identical keys (identical points never dominate
+    // each other and share a front).
+    const bool head = t == 0 || S.sa[t - 1] != my1 || S.sb[t - 1] != my2;
+    const int gstart = block_max_scan(S, head ? t : 0);
+
+    // (2) Fronts. A remaining point is dominated iff some remaining point
+    // sorted before its group has k2 <= its k2.
+    bool rem = real;
     int myrank = 0;
     for (int r = 1;; ++r) {
-        int blocked = 0;
-        if (mine && myrank == 0)
-            for (int w = sub; w < nw; w += kTpp) blocked |= (S.dom[p][w] & S.unassigned[w]) != 0;
-        else
-            blocked = 1;
-        const bool front = point_sum(blocked) == 0;
+        const unsigned long long pm = block_min_scan(S, rem ? my2 : kInf64);
+        S.ia[t] = 0;
+        S.sa[t] = pm;
         __syncthreads();
-        if (front) {
+        const unsigned long long before = gstart > 0 ? S.sa[gstart - 1] : kInf64;
+        const bool in = rem && before > my2;
+        if (in) {
             myrank = r;
-            if (sub == 0) atomicAnd(&S.unassigned[p >> 5], ~(1u << (p & 31)));
+            rem = false;
         }
-        if (!__syncthreads_or(front)) break;
+        __syncthreads();
+        if (!__syncthreads_or(rem)) break;
     }
-    if (mine && sub == 0) S.rank[p] = myrank;
+    if (real) S.rank[id] = myrank;
+    S.ia[t] = id;  // point at sorted position t
+    for (int q = t; q <= kSelThreads; q += blockDim.x) S.fsize[q] = 0;
     __syncthreads();
-    const int per = Npad / kTpp;  // comparison partners per thread (a multiple of 8)
+    if (real) atomicAdd(&S.fsize[myrank], 1);
 
-    // Front offset and size, and the position of p in its front ordered by
-    // (k1, position) and by (k2, position): counting sorts.
-    int below = 0, same = 0, pos1 = 0, pos2 = 0;
-    if (mine) {
-        const long long a1 = S.k1[p], a2 = S.k2[p];
-#pragma unroll 8
-        for (int t = 0; t < per; ++t) {
-            const int q = sub + kTpp * t;
-            const int rq = S.rank[q];
-            const long long b1 = S.k1[q], b2 = S.k2[q];
-            const bool sr = rq == myrank;
-            below += rq < myrank;
-            same += sr;
-            pos1 += sr && ((b1 < a1) || (b1 == a1 && q < p));
-            pos2 += sr && ((b2 < a2) || (b2 == a2 && q < p));
-        }
-    }
-    below = point_sum(below);
-    same = point_sum(same);
-    pos1 = point_sum(pos1);
-    pos2 = point_sum(pos2);
-    if (mine && sub == 0) {
-        S.ord1[below + pos1] = p;
-        S.ord2[below + pos2] = p;
+    // (3) Fronts contiguous, each in (k1, index) order: sort by (rank, position).
+    Key f;
+    f.a = ((real ? (unsigned long long)myrank : 0xffffffffull) << 32) | (unsigned long long)t;
+    f.b = 0;
+    f = block_sort(S, f);
+    const int posA = (int)(f.a & 0xffffffffull);
+    const int e = S.ia[posA];  // point at front-sorted position t
+    const bool ereal = e < N;
+    const int er = ereal ? S.rank[e] : 0;
+    const long long e1 = ereal ? S.k1[e] : 0, e2 = ereal ? S.k2[e] : 0;
+    S.sa[t] = (unsigned long long)e1;
+    S.sb[t] = (unsigned long long)e2;
+    S.ib[t] = er;
+    __syncthreads();
+    const bool fhead = t == 0 || S.ib[t - 1] != er;
+    const int fstart = block_max_scan(S, fhead ? t : 0);
+    const bool ghead = fhead || S.sa[t - 1] != (unsigned long long)e1 || S.sb[t - 1] != (unsigned long long)e2;
+    const int gs = block_max_scan(S, ghead ? t : 0);
+    // End of t's group: the next group head at or after t + 1, via a min scan
+    // over the reversed order.
+    {
+        const int rt = kSelThreads - 1 - t;
+        const bool rhead = rt == kSelThreads - 1 ? true
+                                                 : (S.ib[rt + 1] != S.ib[rt] || S.sa[rt + 1] != S.sa[rt] ||
+                                                    S.sb[rt + 1] != S.sb[rt]);
+        // rhead: position rt + 1 starts a new group (or rt is the last slot)
+        const unsigned long long nh = block_min_scan(S, rhead ? (unsigned long long)(rt + 1) : kInf64);
+        S.ia[rt] = (int)nh;  // first group head after rt
     }
     __syncthreads();
-    if (mine && sub == 0) {
-        const int F = same, off = below;
+    const int ge = S.ia[t];
+    if (ereal) {
+        const int F = S.fsize[er];
+        const int fpos = t - fstart, gsl = gs - fstart, gel = ge - fstart;
         double c;
         if (F <= 2) {
             c = INFINITY;
         } else {
             c = 0.0;
-            if (pos1 == 0 || pos1 == F - 1) {
+            if (fpos == 0 || fpos == F - 1) {
                 c = INFINITY;
             } else {
-                const long long range = S.k1[S.ord1[off + F - 1]] - S.k1[S.ord1[off]];
+                const long long range = (long long)S.sa[fstart + F - 1] - (long long)S.sa[fstart];
                 if (range > 0) {
-                    const long long gap = S.k1[S.ord1[off + pos1 + 1]] - S.k1[S.ord1[off + pos1 - 1]];
+                    const long long gap = (long long)S.sa[t + 1] - (long long)S.sa[t - 1];
                     c = __dadd_rn(c, __ddiv_rn((double)gap, (double)range));
                 }
             }
+            // Objective 2: groups in reverse order, index order inside a group.
+            const int pos2 = (F - gel) + (fpos - gsl);
             if (pos2 == 0 || pos2 == F - 1) {
                 c = INFINITY;
             } else {
-                const long long range = S.k2[S.ord2[off + F - 1]] - S.k2[S.ord2[off]];
+                const long long range = (long long)S.sb[fstart] - (long long)S.sb[fstart + F - 1];
                 if (range > 0) {
-                    const long long gap = S.k2[S.ord2[off + pos2 + 1]] - S.k2[S.ord2[off + pos2 - 1]];
-                    c = __dadd_rn(c, __ddiv_rn((double)gap, (double)range));
+                    const long long lo2 = fpos > gsl ? e2 : (long long)S.sb[ge];
+                    const long long hi2 = fpos < gel - 1 ? e2 : (long long)S.sb[gs - 1];
+                    c = __dadd_rn(c, __ddiv_rn((double)(hi2 - lo2), (double)range));
                 }
             }
         }
-        S.crowd[p] = c;
+        S.crowd[e] = c;
     }
     __syncthreads();
-    // Crowding values are non-negative or +inf (never NaN or -0), so their
-    // IEEE-754 bit patterns order exactly like the values: compare them as
-    // integers rather than on the FP64 pipe.
-    int pos = 0;
-    if (mine) {
-        const unsigned long long c = (unsigned long long)__double_as_longlong(S.crowd[p]);
-#pragma unroll 8
-        for (int t = 0; t < per; ++t) {
-            const int q = sub + kTpp * t;
-            const int rq = S.rank[q];
-            const unsigned long long cq = (unsigned long long)__double_as_longlong(S.crowd[q]);
-            pos += (rq < myrank) || (rq == myrank && (cq > c || (cq == c && q < p)));
-        }
+
+    // (4) Final order by (rank, crowding desc, index). Crowding values are
+    // non-negative or +inf, so their bit patterns order like the values.
+    Key o;
+    {
+        const unsigned long long r = valid ? (unsigned long long)S.rank[t] : 0xffffffffull;
+        const unsigned long long cb = valid ? ~(unsigned long long)__double_as_longlong(S.crowd[t]) : kInf64;
+        o.a = (r << 32) | (cb >> 32);
+        o.b = (cb << 32) | (unsigned long long)t;
     }
-    pos = point_sum(pos);
-    if (mine && sub == 0) S.order[pos] = p;
+    o = block_sort(S, o);
+    S.order[t] = (int)(o.b & 0xffffffffull);
     __syncthreads();
 }
 

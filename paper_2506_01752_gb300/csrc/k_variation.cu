@@ -5,6 +5,8 @@
 // Both kernels work on node-major rows: a warp owns node v; lane q owns the
 // four children 4q..4q+3, which share one Philox call per stage because the
 // stream counter of (child i, node v) is (v, i / 4, g, stage), word i % 4.
+#include <limits.h>
+
 #include "mocd_internal.h"
 #include "philox.cuh"
 
@@ -299,6 +301,19 @@ __device__ __forceinline__ uint32_t hash_slot(int x, int hbits)
     return ((uint32_t)x * 2654435761u) >> (32 - hbits);
 }
 
+// Asynchronous 4-byte global -> shared copy (no register staging) and the
+// wait for all of this thread's outstanding copies.
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 constexpr int kTileStride = 33;  // padded row of the per-warp label tile
 constexpr int kTileRows = 64;    // neighbours whose labels the tile keeps
 constexpr int kMutBlock = 128;   // mutation threads per block (shared memory bound)
@@ -333,16 +348,21 @@ __device__ __forceinline__ int warp_mode(const GenParams &gp, const int32_t *__r
     }
     __syncwarp();
     for (int e0 = 0; e0 < deg; e0 += 32) {
-        if (e0 + lane < deg) {
-            const int x = deg <= kTileRows ? tile_col[(e0 + lane) * kTileStride]
-                                           : child[(size_t)__ldg(col_idx + beg + e0 + lane) * W + i];
+        const bool in = e0 + lane < deg;
+        int x = (int)(0x80000000u | lane);
+        if (in)
+            x = deg <= kTileRows ? tile_col[(e0 + lane) * kTileStride]
+                                 : child[(size_t)__ldg(col_idx + beg + e0 + lane) * W + i];
+        // One insert per distinct label of the chunk, with its multiplicity.
+        const unsigned peers = __match_any_sync(kFull, x);
+        if (in && (peers & ((1u << lane) - 1u)) == 0) {
             uint32_t h = hash_slot(x, hbits);
             // The table holds at most deg < HS / 2 distinct labels, so an empty
             // or matching slot is always found.
             for (int probe = 0; probe < HS; ++probe) {
                 const int prev = atomicCAS(hkey + h, -1, x);
                 if (prev == -1 || prev == x) {
-                    atomicAdd(hcnt + h, 1);
+                    atomicAdd(hcnt + h, __popc(peers));
                     break;
                 }
                 h = (h + 1) & (uint32_t)(HS - 1);
@@ -447,6 +467,7 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
             if (active) reinterpret_cast<int4 *>(s_res)[lane] = out;
             __syncwarp();
             const int my_u0 = lane < deg ? __ldg(col_idx + beg + lane) : 0;
+            const int my_u1 = 32 + lane < deg ? __ldg(col_idx + beg + 32 + lane) : 0;
             bool have_tw = false;
             uint4 tw = make_uint4(0, 0, 0, 0);
             for (int base = 0; base < nsel; base += 32) {
@@ -455,14 +476,41 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                 // count it.
                 const bool has = base + lane < nsel;
                 const int i = has ? s_list[base + lane] : 0;
-                // Pass 1: Boyer-Moore candidate and the count of the node's own
-                // label (usually the strict majority once the population has
-                // converged), eight independent loads in flight; the first 32
-                // neighbours' labels are kept in the tile.
-                const int own = has ? s_res[i] : 0;
-                int cand = 0, run = 0, hits = 0, own_hits = 0;
-                for (int e0 = 0; e0 < deg; e0 += 32) {
-                    const int my_u = e0 == 0 ? my_u0 : (e0 + lane < deg ? __ldg(col_idx + beg + e0 + lane) : 0);
+                // Pass 1: Misra-Gries summary with three counters. The labels of
+                // the first kTileRows neighbours are staged into the tile with
+                // asynchronous copies (all in flight at once), then read from
+                // shared memory. Every label occurring more than deg / 4 times
+                // ends with a positive counter.
+                int c0 = 0, c1 = 0, c2 = 0, n0 = 0, n1 = 0, n2 = 0;
+                auto mg = [&](int x, bool ok) {
+                    // Branch-free update (lanes disagree on the case): match -> +1;
+                    // else the first empty slot takes x; else every counter -1.
+                    const bool m0 = x == c0, m1 = !m0 && x == c1, m2 = !m0 && !m1 && x == c2;
+                    const bool miss = !(m0 || m1 || m2);
+                    const bool f0 = miss && n0 == 0, f1 = miss && !f0 && n1 == 0;
+                    const bool f2 = miss && !f0 && !f1 && n2 == 0;
+                    const int dec = (ok && miss && !f0 && !f1 && !f2) ? 1 : 0;
+                    n0 = ok && (m0 || f0) ? n0 + 1 : n0 - dec;
+                    n1 = ok && (m1 || f1) ? n1 + 1 : n1 - dec;
+                    n2 = ok && (m2 || f2) ? n2 + 1 : n2 - dec;
+                    c0 = ok && f0 ? x : c0;
+                    c1 = ok && f1 ? x : c1;
+                    c2 = ok && f2 ? x : c2;
+                };
+                const int dt = min(deg, kTileRows);
+                for (int j = 0; j < dt; ++j) {
+                    const int u = __shfl_sync(kFull, j < 32 ? my_u0 : my_u1, j & 31);
+                    if (has) cp_async4(tile + j * kTileStride + lane, child + (size_t)u * W + i);
+                }
+                cp_async_wait_all();
+                __syncwarp();
+                if (has) {
+#pragma unroll 4
+                    for (int j = 0; j < dt; ++j) mg(tile[j * kTileStride + lane], true);
+                }
+                // Neighbours beyond the tile: global loads, eight in flight.
+                for (int e0 = kTileRows; e0 < deg; e0 += 32) {
+                    const int my_u = e0 + lane < deg ? __ldg(col_idx + beg + e0 + lane) : 0;
                     const int cnt = min(32, deg - e0);
                     for (int j0 = 0; j0 < cnt; j0 += 8) {
                         int xs[8];
@@ -472,29 +520,21 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                             xs[t] = (has && j0 + t < cnt) ? child[(size_t)u * W + i] : 0;
                         }
 #pragma unroll
-                        for (int t = 0; t < 8; ++t) {
-                            if (has && j0 + t < cnt) {
-                                const int x = xs[t];
-                                own_hits += x == own;
-                                if (run == 0) {
-                                    cand = x;
-                                    run = 1;
-                                } else {
-                                    run += x == cand ? 1 : -1;
-                                }
-                                if (e0 + j0 + t < kTileRows) tile[(e0 + j0 + t) * kTileStride + lane] = x;
-                            }
-                        }
+                        for (int t = 0; t < 8; ++t) mg(xs[t], has && j0 + t < cnt);
                     }
                 }
-                // Pass 2 (only when the own label is not a strict majority and the
-                // candidate differs from it): count the candidate.
-                bool own_wins = has && 2 * own_hits > deg;
-                if (own_wins) cand = own;
-                const bool need2 = has && !own_wins && cand != own;
-                if (need2 && deg <= kTileRows)
-                    for (int j = 0; j < deg; ++j) hits += tile[j * kTileStride + lane] == cand;
-                if (deg > kTileRows && __any_sync(kFull, need2)) {
+                // Pass 2: exact counts of the surviving candidates.
+                const bool v0 = n0 > 0, v1 = n1 > 0, v2 = n2 > 0;
+                int h0 = 0, h1 = 0, h2 = 0;
+                if (has && deg <= kTileRows) {
+                    for (int j = 0; j < deg; ++j) {
+                        const int x = tile[j * kTileStride + lane];
+                        h0 += v0 && x == c0;
+                        h1 += v1 && x == c1;
+                        h2 += v2 && x == c2;
+                    }
+                }
+                if (deg > kTileRows) {
                     for (int e0 = 0; e0 < deg; e0 += 32) {
                         const int my_u = e0 == 0 ? my_u0 : (e0 + lane < deg ? __ldg(col_idx + beg + e0 + lane) : 0);
                         const int cnt = min(32, deg - e0);
@@ -503,17 +543,42 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
 #pragma unroll
                             for (int t = 0; t < 8; ++t) {
                                 const int u = __shfl_sync(kFull, my_u, min(j0 + t, cnt - 1));
-                                xs[t] = (need2 && j0 + t < cnt) ? child[(size_t)u * W + i] : 0;
+                                xs[t] = (has && j0 + t < cnt) ? child[(size_t)u * W + i] : -1;
                             }
 #pragma unroll
-                            for (int t = 0; t < 8; ++t) hits += (need2 && j0 + t < cnt && xs[t] == cand) ? 1 : 0;
+                            for (int t = 0; t < 8; ++t) {
+                                h0 += v0 && xs[t] == c0;
+                                h1 += v1 && xs[t] == c1;
+                                h2 += v2 && xs[t] == c2;
+                            }
                         }
                     }
                 }
-                if (own_wins) hits = own_hits;
+                // If the best candidate count c satisfies 4 c > deg, every label
+                // reaching c is a candidate: the tied set is complete and exact.
+                const int best = max(h0, max(h1, h2));
+                const bool done = has && 4 * best > deg;
+                if (done) {
+                    // Tied candidates in ascending order, then the MTIE pick.
+                    int a = v0 && h0 == best ? c0 : INT_MAX;
+                    int b = v1 && h1 == best ? c1 : INT_MAX;
+                    int c = v2 && h2 == best ? c2 : INT_MAX;
+                    int lo = min(a, b), hi = max(a, b);
+                    a = lo; b = hi;
+                    lo = min(b, c); hi = max(b, c);
+                    b = lo; c = hi;
+                    lo = min(a, b); hi = max(a, b);
+                    a = lo; b = hi;
+                    const int t = 1 + (b != INT_MAX) + (c != INT_MAX);
+                    int lab = a;
+                    if (t > 1) {
+                        const uint4 r = tie_words(gp, v, i >> 2, g);
+                        const uint32_t kk = pick_index(word_of(r, i & 3), (uint32_t)t);
+                        lab = kk == 0 ? a : (kk == 1 ? b : c);
+                    }
+                    s_res[i] = lab;
+                }
                 __syncwarp();
-                const bool done = has && 2 * hits > deg;
-                if (done) s_res[i] = cand;
                 unsigned rest = __ballot_sync(kFull, has && !done);
                 while (rest) {
                     const int l = __ffs(rest) - 1;

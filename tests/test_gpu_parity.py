@@ -139,6 +139,11 @@ def test_init_matches_oracle(gname):
     ("planted-1k", 3, dict(pop_size=33, n_parents=5, p_crossover=1.0, p_mutation=0.0)),
     ("planted-1k", 3, dict(pop_size=31, n_parents=8, p_crossover=0.0, p_mutation=1.0)),
     ("lfr-3k", 4, dict(pop_size=100, seed=5)),
+    # tiny graphs with large populations: many identical keys, multi-member fronts
+    ("appE", 4, dict(pop_size=128)),
+    ("pair", 3, dict(pop_size=100)),
+    ("fig2", 5, dict(pop_size=127, n_parents=2)),
+    ("fig2", 4, dict(pop_size=64, n_parents=7, p_mutation=0.5)),
 ])
 def test_generations_match_oracle(gname, G, kw):
     rp, ci = GRAPHS[gname]()
