@@ -2,8 +2,10 @@
 // Sec. 4.1; Alg. 1 EvaluateIndividual, run for every individual at once).
 //
 // For each individual i the kernel accumulates
-//   intra2_i = #{(v, u) : u in N(v), L_i(v) = L_i(u)}   (= 2 sum_c |E(c)|)
-//   S_i      = sum_c D_c^2,  D_c = sum_{v : L_i(v) = c} deg v
+//   intra_i = #{{v, u} in E : L_i(v) = L_i(u)}   (= sum_c |E(c)|)
+//   S_i     = sum_c D_c^2,  D_c = sum_{v : L_i(v) = c} deg v
+// Each undirected edge is counted once, from its lower endpoint: a warp reads
+// the label rows of the neighbours u > v only, half of the adjacency.
 // exactly in integers. Layout is node-major: a warp owns node v and lane q
 // holds the int4 of labels of individuals 4q..4q+3, so each neighbour u costs
 // one coalesced row read of all individuals' labels instead of N_p scattered
@@ -28,6 +30,7 @@ evaluate_kernel(int n, int W, int count, const int32_t *__restrict__ row_ptr,
 {
     __shared__ unsigned long long s_intra[kMaxPop];
     __shared__ unsigned long long s_sq[kMaxPop];
+    __shared__ int s_nb[kBlock];  // per warp: the chunk's neighbours u > v
     for (int t = threadIdx.x; t < kMaxPop; t += blockDim.x) {
         s_intra[t] = 0;
         s_sq[t] = 0;
@@ -41,6 +44,8 @@ evaluate_kernel(int n, int W, int count, const int32_t *__restrict__ row_ptr,
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int4 *__restrict__ L4 = reinterpret_cast<const int4 *>(labels);
     const int i0 = 4 * lane;
+    int *nb = s_nb + (threadIdx.x & ~31);
+    const unsigned lt = (1u << lane) - 1u;
 
     uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
     unsigned long long q0 = 0, q1 = 0, q2 = 0, q3 = 0;
@@ -53,13 +58,19 @@ evaluate_kernel(int n, int W, int count, const int32_t *__restrict__ row_ptr,
         for (int e0 = beg; e0 < end; e0 += 32) {
             const int cnt = min(32, end - e0);
             const int my_u = lane < cnt ? __ldg(col_idx + e0 + lane) : 0;
+            // Keep the neighbours u > v of this chunk, compacted.
+            const bool up = lane < cnt && my_u > v;
+            const unsigned upm = __ballot_sync(0xffffffffu, up);
+            const int cu = __popc(upm);
+            if (up) nb[__popc(upm & lt)] = my_u;
+            __syncwarp();
             // Four independent row loads in flight per lane.
-            for (int j0 = 0; j0 < cnt; j0 += 4) {
+            for (int j0 = 0; j0 < cu; j0 += 4) {
                 int4 a[4];
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    const int u = __shfl_sync(0xffffffffu, my_u, min(j0 + t, cnt - 1));
-                    a[t] = (active && j0 + t < cnt) ? L4[(size_t)u * nq + lane] : make_int4(-1, -1, -1, -1);
+                    const int u = nb[min(j0 + t, cu - 1)];
+                    a[t] = (active && j0 + t < cu) ? L4[(size_t)u * nq + lane] : make_int4(-1, -1, -1, -1);
                 }
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
@@ -69,6 +80,7 @@ evaluate_kernel(int n, int W, int count, const int32_t *__restrict__ row_ptr,
                     c3 += a[t].w == own.w;
                 }
             }
+            __syncwarp();
         }
         const unsigned long long d = (unsigned long long)(end - beg);
         if (active && d > 0) {

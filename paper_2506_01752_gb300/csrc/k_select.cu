@@ -263,7 +263,7 @@ select_kernel(GenParams gp, PopState ps, int mode)
 
     if (mode == 0) {
         if (p < np) {
-            S.k1[p] = m - (long long)(acc[p] / 2ull);
+            S.k1[p] = m - (long long)acc[p];
             S.k2[p] = (long long)acc[kMaxPop + p];
             S.keep[p] = p;
         }
@@ -274,7 +274,7 @@ select_kernel(GenParams gp, PopState ps, int mode)
             S.k2[p] = ps.pk[kMaxPop + p];
         } else if (p < 2 * np) {
             const int i = p - np;
-            S.k1[p] = m - (long long)(acc[i] / 2ull);
+            S.k1[p] = m - (long long)acc[i];
             S.k2[p] = (long long)acc[kMaxPop + i];
         }
         __syncthreads();

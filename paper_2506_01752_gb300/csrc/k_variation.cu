@@ -162,11 +162,26 @@ crossover_kernel(GenParams gp, const int32_t *buf0, const int32_t *buf1, int32_t
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const bool active = lane < nq;
 
+    // Software pipeline: the next node's rows are requested before the
+    // current node is processed.
+    int4 cur_p = make_int4(0, 0, 0, 0), cur_q = make_int4(0, 0, 0, 0);
+    if (active && warp < gp.n) {
+        cur_p = P4[(size_t)warp * nq + lane];
+        cur_q = Q4[(size_t)warp * nq + lane];
+    }
     for (int v = warp; v < gp.n; v += nwarps) {
-        if (active) {
-            reinterpret_cast<int4 *>(row)[lane] = P4[(size_t)v * nq + lane];
-            reinterpret_cast<int4 *>(row + W)[lane] = Q4[(size_t)v * nq + lane];
+        const int vn = v + nwarps;
+        int4 nxt_p = make_int4(0, 0, 0, 0), nxt_q = make_int4(0, 0, 0, 0);
+        if (active && vn < gp.n) {
+            nxt_p = P4[(size_t)vn * nq + lane];
+            nxt_q = Q4[(size_t)vn * nq + lane];
         }
+        if (active) {
+            reinterpret_cast<int4 *>(row)[lane] = cur_p;
+            reinterpret_cast<int4 *>(row + W)[lane] = cur_q;
+        }
+        cur_p = nxt_p;
+        cur_q = nxt_q;
         __syncwarp();
         if (active && EMAX == 4 && E == 4) {
             // Sort each child's four votes (5 comparators); the run pattern of

@@ -35,7 +35,7 @@ struct PopState {
     int32_t *q;               // Q [n][W]
     int32_t *c;               // post-crossover children [n][W]
     uint32_t *hist;           // [Np][n]
-    unsigned long long *acc;  // [2][kMaxPop]: directed intra count, S
+    unsigned long long *acc;  // [2][kMaxPop]: intra (undirected edges), S
     int64_t *pk;              // [2][kMaxPop]: P keys k1 (m - intra), k2 (S), P order
     int64_t *rk;              // [2][2 kMaxPop]: R keys (P then Q) of the last selection
     int32_t *prank;           // [kMaxPop] rank of P on its own keys (1-based)

@@ -40,7 +40,7 @@ __global__ void finish_keys_kernel(int count, const unsigned long long *__restri
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < count) {
-        intra[i] = (int64_t)(acc[i] / 2ull);
+        intra[i] = (int64_t)acc[i];
         sumsq[i] = (int64_t)acc[kMaxPop + i];
     }
 }

@@ -567,7 +567,7 @@ int mocd_evaluate(mocd_ctx *c, int32_t count, const int32_t *labels, int64_t *in
                            cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
         for (int k = 0; k < b; ++k) {
-            intra[b0 + k] = (int64_t)(acc[k] / 2ull);
+            intra[b0 + k] = (int64_t)acc[k];
             sumsq[b0 + k] = (int64_t)acc[kMaxPop + k];
         }
     }
