@@ -124,6 +124,14 @@ int mocd_get_population(mocd_ctx *ctx, int32_t *labels, int64_t *k1, int64_t *k2
                         int32_t *generation);
 
 /*
+ * Copy out the offspring Q of the most recent generation, in child order
+ * (Alg. 1, the parallel map's output Q^(gen) before environmental selection).
+ *   labels   host int32[N_p * n] or NULL;  k1, k2 host int64[N_p] or NULL
+ * Errors: NOT_READY (no generation has run since initialisation), CUDA.
+ */
+int mocd_get_offspring(mocd_ctx *ctx, int32_t *labels, int64_t *k1, int64_t *k2);
+
+/*
  * Replace the population with caller labels (resume from a checkpoint): the
  * labels are evaluated on the device (Eq. objectives), ranked, and the
  * tournament of generation `generation + 1` is drawn, so a run resumed from

@@ -20,7 +20,7 @@ from . import build as _build
 __all__ = [
     "MocdError", "Params", "Front", "library_path", "load",
     "graph_upload", "population_init", "generation", "pareto_front",
-    "get_population", "set_population", "evaluate", "synchronize",
+    "get_population", "get_offspring", "set_population", "evaluate", "synchronize",
     "set_timing", "kernel_times", "info", "destroy", "status_string", "evaluate_noalloc",
     "STAGES",
 ]
@@ -93,6 +93,7 @@ def load():
         "mocd_generation": (ctypes.c_int, [P, i32]),
         "mocd_pareto_front": (ctypes.c_int, [P, i32, P, P, P, P, P, P, P]),
         "mocd_get_population": (ctypes.c_int, [P, P, P, P, P]),
+        "mocd_get_offspring": (ctypes.c_int, [P, P, P, P]),
         "mocd_set_population": (ctypes.c_int, [P, ctypes.POINTER(_CParams), P, i32]),
         "mocd_evaluate": (ctypes.c_int, [P, i32, P, P, P]),
         "mocd_synchronize": (ctypes.c_int, [P]),
@@ -186,6 +187,16 @@ def get_population(ctx):
     g = ctypes.c_int32()
     _check(load().mocd_get_population(ctx, _p(labels), _p(k1), _p(k2), ctypes.byref(g)), "mocd_get_population")
     return labels, k1, k2, g.value
+
+
+def get_offspring(ctx):
+    """(labels [N_p][n], k1, k2) of the most recent generation's children Q."""
+    d = info(ctx)
+    labels = np.zeros((d["pop_size"], d["n"]), dtype=np.int32)
+    k1 = np.zeros(d["pop_size"], dtype=np.int64)
+    k2 = np.zeros(d["pop_size"], dtype=np.int64)
+    _check(load().mocd_get_offspring(ctx, _p(labels), _p(k1), _p(k2)), "mocd_get_offspring")
+    return labels, k1, k2
 
 
 def set_population(ctx, params: Params, labels, generation: int = 0):

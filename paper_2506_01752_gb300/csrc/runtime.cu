@@ -312,24 +312,19 @@ int validate_labels(const mocd_ctx *c, const int32_t *labels, size_t count)
     return MOCD_OK;
 }
 
-// Individual-major labels of `count` P positions (pos NULL: all of P).
-int download_members(mocd_ctx *c, const int32_t *pos_host, int count, int32_t *labels)
+// Individual-major labels of `count` members of R = (P half, Q), given by
+// their R indices on the host.
+int download_r(mocd_ctx *c, const int32_t *ridx, int count, int32_t *labels)
 {
     if (count <= 0 || !labels) return MOCD_OK;
     int rc = grow(&c->d_im, &c->im_cap, (size_t)count * (size_t)c->n);
     if (rc) return rc;
-    std::vector<int32_t> keep(c->gp.np);
-    CK(cudaMemcpyAsync(keep.data(), c->ps.keep, sizeof(int32_t) * c->gp.np, cudaMemcpyDeviceToHost,
-                       c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    std::vector<int32_t> ridx(count);
-    for (int k = 0; k < count; ++k) ridx[k] = keep[pos_host ? pos_host[k] : k];
     if (!c->d_idx) {
         void *q = nullptr;
-        CK(cudaMalloc(&q, sizeof(int32_t) * kMaxPop));
+        CK(cudaMalloc(&q, sizeof(int32_t) * 2 * kMaxPop));
         c->d_idx = static_cast<int32_t *>(q);
     }
-    CK(cudaMemcpyAsync(c->d_idx, ridx.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_idx, ridx, sizeof(int32_t) * count, cudaMemcpyHostToDevice, c->stream));
     const int32_t *phalf = c->ps.buf[(uint32_t)(c->host_gen + 1) & 1u];
     CK(launch_gather_individuals((int)c->n, c->W, c->gp.np, phalf, c->ps.q, c->d_idx, count, c->d_im,
                                  c->stream));
@@ -337,6 +332,19 @@ int download_members(mocd_ctx *c, const int32_t *pos_host, int count, int32_t *l
                        cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return MOCD_OK;
+}
+
+// Individual-major labels of `count` P positions (pos NULL: all of P).
+int download_members(mocd_ctx *c, const int32_t *pos_host, int count, int32_t *labels)
+{
+    if (count <= 0 || !labels) return MOCD_OK;
+    std::vector<int32_t> keep(c->gp.np);
+    CK(cudaMemcpyAsync(keep.data(), c->ps.keep, sizeof(int32_t) * c->gp.np, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    std::vector<int32_t> ridx(count);
+    for (int k = 0; k < count; ++k) ridx[k] = keep[pos_host ? pos_host[k] : k];
+    return download_r(c, ridx.data(), count, labels);
 }
 
 }  // namespace
@@ -532,6 +540,24 @@ int mocd_get_population(mocd_ctx *c, int32_t *labels, int64_t *k1, int64_t *k2, 
     }
     if (generation) *generation = c->host_gen;
     return download_members(c, nullptr, np, labels);
+}
+
+int mocd_get_offspring(mocd_ctx *c, int32_t *labels, int64_t *k1, int64_t *k2)
+{
+    if (!c) return MOCD_ERR_INVALID_ARG;
+    if (!c->ready || c->host_gen < 1) return MOCD_ERR_NOT_READY;
+    CK(cudaSetDevice(c->device));
+    const int np = c->gp.np;
+    std::vector<int64_t> rk(4 * kMaxPop);
+    CK(cudaMemcpyAsync(rk.data(), c->ps.rk, sizeof(int64_t) * 4 * kMaxPop, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < np; ++i) {
+        if (k1) k1[i] = rk[np + i];
+        if (k2) k2[i] = rk[2 * kMaxPop + np + i];
+    }
+    std::vector<int32_t> ridx(np);
+    for (int i = 0; i < np; ++i) ridx[i] = np + i;
+    return download_r(c, ridx.data(), np, labels);
 }
 
 int mocd_evaluate(mocd_ctx *c, int32_t count, const int32_t *labels, int64_t *intra, int64_t *sumsq)

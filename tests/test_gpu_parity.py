@@ -250,3 +250,41 @@ def test_invalid_params_rejected():
         with pytest.raises(mocd.MocdError) as e:
             mocd.generation(h, 1)
         assert e.value.status == -9
+
+
+def test_offspring_match_oracle():
+    """Q of generations 1 and 2 (child order, before selection) and their keys."""
+    rp, ci = GRAPHS["lfr-3k"]()
+    gp, op = _params(pop_size=64, seed=8)
+    st = oracle.population_init(rp, ci, op)
+    with Ctx(rp, ci) as h:
+        mocd.population_init(h, gp)
+        with pytest.raises(mocd.MocdError):
+            mocd.get_offspring(h)  # no generation yet
+        for gen in (1, 2):
+            mocd.generation(h, 1)
+            q, qk1, qk2 = mocd.get_offspring(h)
+            Q, rk1, rk2 = oracle.make_offspring(rp, ci, op, gen, st)
+            assert np.array_equal(q, Q) and np.array_equal(qk1, rk1) and np.array_equal(qk2, rk2)
+            st = oracle.run(rp, ci, op, st, 1)
+
+
+def test_full_size_1m_sampled():
+    """The large workload (n = 10^6, m ~ 7.9M, maximum degree 200) in the
+    engine's own launch configuration: the whole initial population and its
+    keys, then sampled children of generation 1, bit for bit."""
+    rp, ci, _ = synth.workload("lfr-1m", seed=0)
+    gp, op = _params(seed=0)
+    with Ctx(rp, ci) as h:
+        mocd.population_init(h, gp)
+        p0, k1, k2, _ = mocd.get_population(h)
+        mocd.generation(h, 1)
+        q, qk1, qk2 = mocd.get_offspring(h)
+    st = oracle.population_init(rp, ci, op)
+    assert np.array_equal(k1, st.k1) and np.array_equal(k2, st.k2)
+    assert np.array_equal(p0, st.labels)
+    del p0
+    for i in (0, 57, 99):
+        Q, rk1, rk2 = oracle.make_offspring_range(rp, ci, op, 1, st, i, i + 1)
+        assert np.array_equal(q[i], Q[i]), f"child {i} differs"
+        assert qk1[i] == rk1[i] and qk2[i] == rk2[i]
