@@ -330,7 +330,7 @@ __device__ __forceinline__ void cp_async_wait_all()
 }
 
 constexpr int kTileStride = 33;  // padded row of the per-warp label tile
-constexpr int kTileRows = 64;    // neighbours whose labels the tile keeps
+constexpr int kTileRows = 32;    // neighbours whose labels the tile keeps
 constexpr int kMutBlock = 128;   // mutation threads per block (shared memory bound)
 
 // Exact neighbour-majority of one (node, child) pair by the whole warp

@@ -52,7 +52,7 @@ def test_algorithmic_bytes():
     b = bench.algorithmic_bytes(n=1000, m=5000, np_=100, p_mut=0.2)
     csr = 4 * 1001 + 4 * 10000
     assert b["crossover"] == 16 * 100 * 1000
-    assert b["evaluate"] == 4 * 100 * 1000 + 4 * 100 * 10000 + 8 * 100 * 1000 + csr
+    assert b["evaluate"] == 4 * 100 * 1000 + 4 * 100 * 5000 + 8 * 100 * 1000 + csr
     assert b["mutation"] == 8 * 100 * 1000 + 4 * 0.2 * 100 * 10000 + csr + 4 * 100 * 1000
 
 
