@@ -187,6 +187,40 @@ int mocd_evaluate_noalloc(const int32_t *row_ptr, const int32_t *col_idx, int64_
                           const int32_t *labels, int32_t count, int64_t *intra, int64_t *sumsq,
                           void *cuda_stream);
 
+/*
+ * Batched generations of several independent instances -- a deployment form,
+ * not a step of the paper (whose Alg. 1 evolves one population). A batch
+ * groups initialised contexts on one device; each generation of all of them
+ * is ONE CUDA-graph launch in which the per-instance kernel chains
+ * (crossover, mutation, evaluation, selection) run concurrently, so small
+ * instances and the one-block selection steps of different instances share
+ * the GPU. Every instance's results are bit-identical to running it alone.
+ *   mocd_batch_create   ctxs: `count` contexts, each initialised
+ *                       (mocd_population_init or mocd_set_population), all on
+ *                       the current device; the batch does not own them and
+ *                       must be destroyed before them. cuda_stream: stream for
+ *                       the batch launches, or NULL for one the batch owns.
+ *                       Errors: INVALID_ARG, NOT_READY, CUDA.
+ *   mocd_batch_generation  n_generations generations of every instance,
+ *                       asynchronous on the batch stream. Call
+ *                       mocd_batch_synchronize before using a member context
+ *                       (its own calls run on its own stream). Re-initialising
+ *                       a member invalidates the batch (NOT_READY).
+ *   mocd_batch_autotune picks the launch shape (nodes per warp of the node
+ *                       kernels, one of 1, 2, 4, 8, 16) with the shortest
+ *                       measured batch generation; each trial runs
+ *                       `generations_per_trial` generations, so the
+ *                       populations advance (re-initialise afterwards for a
+ *                       run from generation 0). Results never depend on the
+ *                       launch shape. Writes the choice to *nodes_per_warp.
+ */
+typedef struct mocd_batch mocd_batch;
+int mocd_batch_create(mocd_batch **out, int32_t count, mocd_ctx *const *ctxs, void *cuda_stream);
+int mocd_batch_generation(mocd_batch *b, int32_t n_generations);
+int mocd_batch_autotune(mocd_batch *b, int32_t generations_per_trial, int32_t *nodes_per_warp);
+int mocd_batch_synchronize(mocd_batch *b);
+void mocd_batch_destroy(mocd_batch *b);
+
 /* Block until all work issued on the context stream is done. */
 int mocd_synchronize(mocd_ctx *ctx);
 

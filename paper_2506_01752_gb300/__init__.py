@@ -22,6 +22,7 @@ __all__ = [
     "graph_upload", "population_init", "generation", "pareto_front",
     "get_population", "get_offspring", "set_population", "evaluate", "synchronize",
     "set_timing", "kernel_times", "info", "destroy", "status_string", "evaluate_noalloc",
+    "batch_create", "batch_generation", "batch_autotune", "batch_synchronize", "batch_destroy",
     "STAGES",
 ]
 
@@ -103,6 +104,11 @@ def load():
         "mocd_destroy": (None, [P]),
         "mocd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "mocd_evaluate_noalloc": (ctypes.c_int, [P, P, i64, P, i32, P, P, P]),
+        "mocd_batch_create": (ctypes.c_int, [ctypes.POINTER(P), i32, P, P]),
+        "mocd_batch_generation": (ctypes.c_int, [P, i32]),
+        "mocd_batch_autotune": (ctypes.c_int, [P, i32, P]),
+        "mocd_batch_synchronize": (ctypes.c_int, [P]),
+        "mocd_batch_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -226,6 +232,37 @@ def evaluate_noalloc(row_ptr_dev: int, col_idx_dev: int, n: int, labels_dev: int
     is asynchronous on ``stream``."""
     _check(load().mocd_evaluate_noalloc(row_ptr_dev, col_idx_dev, int(n), labels_dev, int(count), intra_dev,
                                         sumsq_dev, _stream_handle(stream)), "mocd_evaluate_noalloc")
+
+
+def batch_create(ctxs, stream=None):
+    """Group initialised contexts; one CUDA-graph launch then runs a
+    generation of every one of them (see mocd_batch_create)."""
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    b = ctypes.c_void_p()
+    _check(load().mocd_batch_create(ctypes.byref(b), len(ctxs), ctypes.cast(arr, ctypes.c_void_p),
+                                    _stream_handle(stream)), "mocd_batch_create")
+    b._members = list(ctxs)
+    return b
+
+
+def batch_generation(b, n_generations: int = 1):
+    _check(load().mocd_batch_generation(b, int(n_generations)), "mocd_batch_generation")
+
+
+def batch_autotune(b, generations_per_trial: int = 3) -> int:
+    out = ctypes.c_int32()
+    _check(load().mocd_batch_autotune(b, int(generations_per_trial), ctypes.byref(out)), "mocd_batch_autotune")
+    return out.value
+
+
+def batch_synchronize(b):
+    _check(load().mocd_batch_synchronize(b), "mocd_batch_synchronize")
+
+
+def batch_destroy(b):
+    if b is not None and b.value:
+        load().mocd_batch_destroy(b)
+        b.value = None
 
 
 def synchronize(ctx):

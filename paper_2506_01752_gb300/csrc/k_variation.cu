@@ -669,6 +669,11 @@ int mutation_smem(int hash_size)
     return (kMutBlock / 32) * (2 * kMaxPop + kTileRows * kTileStride + 2 * hash_size) * (int)sizeof(int);
 }
 
+int mutation_warps_per_block()
+{
+    return kMutBlock / 32;
+}
+
 int grid_for_mutation(int sms, int hash_size, int *smem_bytes)
 {
     const int smem = mutation_smem(hash_size);

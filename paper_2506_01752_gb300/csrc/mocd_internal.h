@@ -85,5 +85,6 @@ cudaError_t launch_to_node_major(int n, int W, int count, const int32_t *src, in
 int grid_for_eval(int sms);
 int grid_for_crossover(int sms, int es);
 int grid_for_mutation(int sms, int hash_size, int *smem_bytes);
+int mutation_warps_per_block();
 
 }  // namespace mocd

@@ -46,7 +46,10 @@ struct mocd_ctx {
     size_t hist_cap = 0;    // entries of ps.hist
     void *d_small = nullptr;
     int grid_eval = 0, grid_cross = 0, grid_mut = 0;
+    int occ_eval = 0, occ_cross = 0, occ_mut = 0;  // occupancy-limited grids
+    int nodes_per_warp = 1;                         // launch shape (autotuned for batches)
     int32_t host_gen = 0;   // generations run since init
+    int32_t version = 0;    // bumped whenever the population is (re)built
     uint32_t gen_host_value = 0;
 
     cudaGraph_t graph = nullptr;
@@ -137,6 +140,23 @@ int check_params(const mocd_ctx *c, const mocd_params *p)
     return MOCD_OK;
 }
 
+// Grids of the node-parallel kernels: enough warps for nodes_per_warp nodes
+// each, never more than fit on the GPU at once (the kernels stride over the
+// remaining nodes). Small graphs get small grids, which matters when several
+// instances share the GPU.
+void size_grids(mocd_ctx *c)
+{
+    const long long n = c->n;
+    auto shape = [&](int occ, int warps_per_block) {
+        const long long per_block = (long long)warps_per_block * c->nodes_per_warp;
+        const long long want = (n + per_block - 1) / per_block;
+        return (int)std::max<long long>(1, std::min<long long>(occ, want));
+    };
+    c->grid_eval = shape(c->occ_eval, kBlock / 32);
+    c->grid_cross = shape(c->occ_cross, kBlock / 32);
+    c->grid_mut = shape(c->occ_mut, mutation_warps_per_block());
+}
+
 // Allocate (or reuse) the population buffers for params and fill gp / ps.
 int prepare_population(mocd_ctx *c, const mocd_params *p)
 {
@@ -205,6 +225,7 @@ int prepare_population(mocd_ctx *c, const mocd_params *p)
     }
     c->W = W;
     c->params = *p;
+    c->version += 1;
     GenParams &gp = c->gp;
     gp.n = (int)c->n;
     gp.W = W;
@@ -222,10 +243,11 @@ int prepare_population(mocd_ctx *c, const mocd_params *p)
     gp.key1 = (uint32_t)(p->seed >> 32);
     gp.thr_c = (unsigned long long)floor(p->p_crossover * 4294967296.0);
     gp.thr_m = (unsigned long long)floor(p->p_mutation * 4294967296.0);
-    c->grid_eval = grid_for_eval(c->sms);
-    c->grid_cross = grid_for_crossover(c->sms, gp.es);
+    c->occ_eval = grid_for_eval(c->sms);
+    c->occ_cross = grid_for_crossover(c->sms, gp.es);
     int smem = 0;
-    c->grid_mut = grid_for_mutation(c->sms, gp.hash_size, &smem);
+    c->occ_mut = grid_for_mutation(c->sms, gp.hash_size, &smem);
+    size_grids(c);
     return MOCD_OK;
 }
 
@@ -237,27 +259,27 @@ int clear_eval_state(mocd_ctx *c, uint32_t *hist, size_t hist_entries, unsigned 
 }
 
 // Timing events become event-record nodes of the captured graph.
-cudaError_t mark(mocd_ctx *c, int k)
+cudaError_t mark(mocd_ctx *c, int k, cudaStream_t st)
 {
-    return cudaEventRecordWithFlags(c->ev[k], c->stream, cudaEventRecordExternal);
+    return cudaEventRecordWithFlags(c->ev[k], st, cudaEventRecordExternal);
 }
 
-// One generation of Alg. 1 on the context stream. The mutation kernel also
-// clears the histogram and accumulators that the evaluation then fills.
-int issue_generation(mocd_ctx *c, bool events)
+// One generation of Alg. 1 on stream st. The mutation kernel also clears the
+// histogram and accumulators that the evaluation then fills.
+int issue_generation(mocd_ctx *c, cudaStream_t st, bool events)
 {
     const GenParams &gp = c->gp;
     const PopState &ps = c->ps;
-    if (events) CK(mark(c, 0));
-    CK(launch_crossover(gp, ps, c->grid_cross, c->stream));
-    if (events) CK(mark(c, 1));
-    CK(launch_mutation(gp, ps, c->d_row_ptr, c->d_col_idx, c->d_order, c->grid_mut, c->stream));
-    if (events) CK(mark(c, 2));
+    if (events) CK(mark(c, 0, st));
+    CK(launch_crossover(gp, ps, c->grid_cross, st));
+    if (events) CK(mark(c, 1, st));
+    CK(launch_mutation(gp, ps, c->d_row_ptr, c->d_col_idx, c->d_order, c->grid_mut, st));
+    if (events) CK(mark(c, 2, st));
     CK(launch_evaluate(gp.n, gp.W, gp.np, c->d_row_ptr, c->d_col_idx, ps.q, ps.hist, ps.acc,
-                       c->grid_eval, c->stream, c->d_order));
-    if (events) CK(mark(c, 3));
-    CK(launch_select(gp, ps, 1, c->stream));
-    if (events) CK(mark(c, 4));
+                       c->grid_eval, st, c->d_order));
+    if (events) CK(mark(c, 3, st));
+    CK(launch_select(gp, ps, 1, st));
+    if (events) CK(mark(c, 4, st));
     return MOCD_OK;
 }
 
@@ -268,7 +290,7 @@ int build_graph(mocd_ctx *c)
     c->graph_exec = nullptr;
     c->graph = nullptr;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    int rc = issue_generation(c, c->timing);
+    int rc = issue_generation(c, c->stream, c->timing);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (rc) {
@@ -638,6 +660,169 @@ int mocd_info(mocd_ctx *c, int64_t *n, int64_t *m, int32_t *pop_size, int32_t *g
     if (pop_size) *pop_size = c->ready ? c->gp.np : 0;
     if (generation) *generation = c->host_gen;
     return MOCD_OK;
+}
+
+struct mocd_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<mocd_ctx *> ctx;
+    std::vector<int32_t> version;
+    std::vector<cudaStream_t> branch;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+static int batch_build(mocd_batch *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = MOCD_OK;
+    cudaError_t e = cudaEventRecord(b->fork, b->stream);
+    for (size_t i = 0; i < b->ctx.size() && rc == MOCD_OK && e == cudaSuccess; ++i) {
+        e = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
+        if (e == cudaSuccess) rc = issue_generation(b->ctx[i], b->branch[i], false);
+        if (rc == MOCD_OK && e == cudaSuccess) e = cudaEventRecord(b->join[i], b->branch[i]);
+        if (rc == MOCD_OK && e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join[i], 0);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (rc || e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return rc ? rc : cuda_status(e != cudaSuccess ? e : e2);
+    }
+    b->graph = g;
+    CK(cudaGraphInstantiate(&b->exec, g, 0));
+    return MOCD_OK;
+}
+
+int mocd_batch_create(mocd_batch **out, int32_t count, mocd_ctx *const *ctxs, void *cuda_stream)
+{
+    if (!out) return MOCD_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (count < 1 || !ctxs) return MOCD_ERR_INVALID_ARG;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    for (int32_t i = 0; i < count; ++i) {
+        if (!ctxs[i]) return MOCD_ERR_INVALID_ARG;
+        if (ctxs[i]->device != dev) return MOCD_ERR_INVALID_ARG;
+        if (!ctxs[i]->ready) return MOCD_ERR_NOT_READY;
+        for (int32_t j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return MOCD_ERR_INVALID_ARG;
+    }
+    mocd_batch *b = new (std::nothrow) mocd_batch();
+    if (!b) return MOCD_ERR_OUT_OF_MEMORY;
+    b->device = dev;
+    auto fail = [&](int rc) {
+        mocd_batch_destroy(b);
+        return rc;
+    };
+    if (cuda_stream) {
+        b->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(MOCD_ERR_CUDA);
+        b->own_stream = true;
+    }
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return fail(MOCD_ERR_CUDA);
+    for (int32_t i = 0; i < count; ++i) {
+        // Work already issued on a member's own stream finishes first.
+        if (cudaStreamSynchronize(ctxs[i]->stream) != cudaSuccess) return fail(MOCD_ERR_CUDA);
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return fail(MOCD_ERR_CUDA);
+        b->branch.push_back(st);
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return fail(MOCD_ERR_CUDA);
+        b->join.push_back(ev);
+        b->ctx.push_back(ctxs[i]);
+        b->version.push_back(ctxs[i]->version);
+    }
+    const int rc = batch_build(b);
+    if (rc) return fail(rc);
+    *out = b;
+    return MOCD_OK;
+}
+
+int mocd_batch_generation(mocd_batch *b, int32_t n_generations)
+{
+    if (!b || n_generations < 0) return MOCD_ERR_INVALID_ARG;
+    for (size_t i = 0; i < b->ctx.size(); ++i)
+        if (!b->ctx[i]->ready || b->ctx[i]->version != b->version[i]) return MOCD_ERR_NOT_READY;
+    for (int32_t k = 0; k < n_generations; ++k) CK(cudaGraphLaunch(b->exec, b->stream));
+    for (mocd_ctx *c : b->ctx) {
+        c->host_gen += n_generations;
+        c->timing_valid = false;
+    }
+    return MOCD_OK;
+}
+
+int mocd_batch_synchronize(mocd_batch *b)
+{
+    if (!b) return MOCD_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(b->stream));
+    return MOCD_OK;
+}
+
+int mocd_batch_autotune(mocd_batch *b, int32_t generations_per_trial, int32_t *nodes_per_warp)
+{
+    if (!b || generations_per_trial < 1) return MOCD_ERR_INVALID_ARG;
+    static const int kShapes[] = {1, 2, 4, 8, 16};
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    CK(cudaEventCreate(&t0));
+    CK(cudaEventCreate(&t1));
+    float best_ms = 0.0f;
+    int best = 1;
+    int rc = MOCD_OK;
+    for (int shape : kShapes) {
+        for (mocd_ctx *c : b->ctx) {
+            c->nodes_per_warp = shape;
+            size_grids(c);
+        }
+        if ((rc = batch_build(b))) break;
+        if ((rc = mocd_batch_generation(b, 1))) break;  // warm-up
+        if (cudaEventRecord(t0, b->stream) != cudaSuccess) { rc = MOCD_ERR_CUDA; break; }
+        if ((rc = mocd_batch_generation(b, generations_per_trial))) break;
+        if (cudaEventRecord(t1, b->stream) != cudaSuccess || cudaEventSynchronize(t1) != cudaSuccess) {
+            rc = MOCD_ERR_CUDA;
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, t0, t1);
+        if (shape == kShapes[0] || ms < best_ms) {
+            best_ms = ms;
+            best = shape;
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (rc) return rc;
+    for (mocd_ctx *c : b->ctx) {
+        c->nodes_per_warp = best;
+        size_grids(c);
+        // Keep each member's own generation graph in the same launch shape.
+        if ((rc = build_graph(c))) return rc;
+    }
+    if ((rc = batch_build(b))) return rc;
+    if (nodes_per_warp) *nodes_per_warp = best;
+    return MOCD_OK;
+}
+
+void mocd_batch_destroy(mocd_batch *b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaStream_t st : b->branch) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->join) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
 }
 
 void mocd_destroy(mocd_ctx *c)

@@ -1,0 +1,87 @@
+"""Batched generations (several instances, one CUDA-graph launch per
+generation): every instance must evolve exactly as it does alone, which the
+oracle pins."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2506_01752_gb300 as mocd
+import synth
+from _golden import graph, load
+
+pytestmark = pytest.mark.gpu
+
+
+def _instances():
+    return [
+        (synth.workload("planted-1k", seed=0)[:2], dict(pop_size=100, seed=1)),
+        (synth.lfr_style(3000, 20, 50, 0.3, seed=2)[:2], dict(pop_size=64, seed=2)),
+        (graph(load("appE_operator_example.txt")), dict(pop_size=8, n_parents=3, seed=3)),
+        (synth.lfr_style(1500, 12, 60, 0.4, seed=4)[:2], dict(pop_size=100, seed=4, p_mutation=0.5)),
+        (graph(load("fig2_toy_graph.txt")), dict(pop_size=33, n_parents=5, seed=5)),
+    ]
+
+
+def _run(autotune):
+    inst = _instances()
+    ctxs = [mocd.graph_upload(rp, ci) for (rp, ci), _ in inst]
+    try:
+        for c, (_, kw) in zip(ctxs, inst):
+            mocd.population_init(c, mocd.Params(**kw))
+        b = mocd.batch_create(ctxs)
+        try:
+            if autotune:
+                shape = mocd.batch_autotune(b, 2)
+                assert shape in (1, 2, 4, 8, 16)
+                mocd.batch_synchronize(b)
+                # the members advanced during tuning: start them again
+                for c, (_, kw) in zip(ctxs, inst):
+                    mocd.population_init(c, mocd.Params(**kw))
+                with pytest.raises(mocd.MocdError) as e:
+                    mocd.batch_generation(b, 1)
+                assert e.value.status == -9
+                mocd.batch_destroy(b)
+                b = mocd.batch_create(ctxs)
+            mocd.batch_generation(b, 4)
+            mocd.batch_synchronize(b)
+            for c, ((rp, ci), kw) in zip(ctxs, inst):
+                op = oracle.Params(**kw)
+                ref = oracle.run(rp, ci, op, oracle.population_init(rp, ci, op), 4)
+                labels, k1, k2, gen = mocd.get_population(c)
+                assert gen == 4
+                assert np.array_equal(k1, ref.k1) and np.array_equal(k2, ref.k2)
+                assert np.array_equal(labels, ref.labels)
+            # a member keeps working on its own after batch generations
+            mocd.generation(ctxs[0], 1)
+            (rp, ci), kw = inst[0]
+            op = oracle.Params(**kw)
+            ref = oracle.run(rp, ci, op, oracle.population_init(rp, ci, op), 5)
+            assert np.array_equal(mocd.get_population(ctxs[0])[0], ref.labels)
+        finally:
+            mocd.batch_destroy(b)
+    finally:
+        for c in ctxs:
+            mocd.destroy(c)
+
+
+def test_batch_matches_oracle():
+    _run(autotune=False)
+
+
+def test_batch_after_autotune_matches_oracle():
+    _run(autotune=True)
+
+
+def test_batch_rejects_bad_members():
+    rp, ci = graph(load("fig2_toy_graph.txt"))
+    c = mocd.graph_upload(rp, ci)
+    try:
+        with pytest.raises(mocd.MocdError) as e:
+            mocd.batch_create([c])  # not initialised
+        assert e.value.status == -9
+        mocd.population_init(c, mocd.Params(pop_size=10))
+        with pytest.raises(mocd.MocdError) as e:
+            mocd.batch_create([c, c])  # repeated member
+        assert e.value.status == -1
+    finally:
+        mocd.destroy(c)
