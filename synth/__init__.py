@@ -11,6 +11,7 @@ from .graphs import (  # noqa: F401
     planted_partition,
     lfr_style,
     random_labels,
+    batch_instances,
     workload,
     WORKLOADS,
 )

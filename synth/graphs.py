@@ -245,6 +245,34 @@ def random_labels(n: int, count: int, seed: int, n_distinct: int | None = None):
     return ids[rng.integers(0, ids.size, size=(count, n))].astype(np.int32)
 
 
+def batch_instances(count: int = 64, seed: int = 0):
+    """Many uneven detection jobs: n log-uniform in [1e3, 5e4], average degree
+    uniform in [10, 30], mixing mu uniform in [0.2, 0.5]; even-numbered jobs are
+    planted-partition graphs (communities of 20-100 nodes), odd ones
+    LFR-style graphs (maximum degree 2.5x the average). Returns a list of
+    (row_ptr, col_idx, truth, description)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(1e3), math.log(5e4)))))
+        d = float(rng.uniform(10, 30))
+        mu = float(rng.uniform(0.2, 0.5))
+        s = int(rng.integers(0, 1 << 31))
+        if k % 2 == 0:
+            size = int(rng.integers(20, 101))
+            n_comm = max(2, n // size)
+            nn = n_comm * size
+            p_in = min(1.0, (1 - mu) * d / (size - 1))
+            p_out = mu * d / (nn - size)
+            rp, ci, tr = planted_partition(n_comm, size, p_in, p_out, seed=s)
+            desc = f"planted n={nn} d={d:.1f} mu={mu:.2f}"
+        else:
+            rp, ci, tr = lfr_style(n, d, int(round(2.5 * d)), mu, seed=s)
+            desc = f"lfr n={n} d={d:.1f} mu={mu:.2f}"
+        out.append((rp, ci, tr, desc))
+    return out
+
+
 # Named workloads: shapes of the paper's experiments (Sec. 5.2, Table of
 # parameters: N_p = 100, G = 100, C_P = 0.8, M_P = 0.2, E_S = 4).
 WORKLOADS = {
