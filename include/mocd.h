@@ -221,6 +221,39 @@ int mocd_batch_autotune(mocd_batch *b, int32_t generations_per_trial, int32_t *n
 int mocd_batch_synchronize(mocd_batch *b);
 void mocd_batch_destroy(mocd_batch *b);
 
+/*
+ * Continuous-batching detection server -- a deployment form, not a step of the
+ * paper. Jobs (a graph, parameters and a generation count) are queued by
+ * mocd_server_submit; each mocd_server_step call (a scheduling round):
+ *   1. retires running jobs whose last generation has completed: their Pareto
+ *      front (as mocd_pareto_front returns it) is kept for mocd_server_result
+ *      and their device memory is released;
+ *   2. admits queued jobs in submission order while the estimated device
+ *      footprint of the running jobs stays within hbm_budget_bytes and fewer
+ *      than max_running jobs run (a job larger than the whole budget fails
+ *      with OUT_OF_MEMORY); admission uploads the graph and initialises the
+ *      population (host work, blocking);
+ *   3. issues up to `depth` further generations of every running job, each job
+ *      on its own CUDA stream, so running jobs share the GPU concurrently.
+ * A job's result depends only on its own inputs: it is identical alone and in
+ * any mix. mocd_server_step never blocks on the GPU except to copy finished
+ * fronts; call it in a loop.
+ *   mocd_server_submit  copies the host CSR (validated at admission); the
+ *                       job id is written to *job_id (ids start at 1).
+ *   mocd_server_job_state  *state: 0 queued, 1 running, 2 done, 3 failed
+ *                       (*status then holds the MOCD_ERR_* code).
+ *   mocd_server_result  as mocd_pareto_front, for a done job.
+ */
+typedef struct mocd_server mocd_server;
+int mocd_server_create(mocd_server **out, int64_t hbm_budget_bytes, int32_t max_running, int32_t depth);
+int mocd_server_submit(mocd_server *s, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                       const mocd_params *params, int32_t generations, int64_t *job_id);
+int mocd_server_step(mocd_server *s, int32_t *running, int32_t *queued, int32_t *done);
+int mocd_server_job_state(mocd_server *s, int64_t job_id, int32_t *state, int32_t *status);
+int mocd_server_result(mocd_server *s, int64_t job_id, int32_t cap, int32_t *count, int32_t *labels,
+                       double *f1, double *f2, int64_t *intra, int64_t *sumsq, int32_t *best);
+void mocd_server_destroy(mocd_server *s);
+
 /* Block until all work issued on the context stream is done. */
 int mocd_synchronize(mocd_ctx *ctx);
 

@@ -23,6 +23,7 @@ __all__ = [
     "get_population", "get_offspring", "set_population", "evaluate", "synchronize",
     "set_timing", "kernel_times", "info", "destroy", "status_string", "evaluate_noalloc",
     "batch_create", "batch_generation", "batch_autotune", "batch_synchronize", "batch_destroy",
+    "Server",
     "STAGES",
 ]
 
@@ -109,6 +110,12 @@ def load():
         "mocd_batch_autotune": (ctypes.c_int, [P, i32, P]),
         "mocd_batch_synchronize": (ctypes.c_int, [P]),
         "mocd_batch_destroy": (None, [P]),
+        "mocd_server_create": (ctypes.c_int, [ctypes.POINTER(P), i64, i32, i32]),
+        "mocd_server_submit": (ctypes.c_int, [P, i64, P, P, ctypes.POINTER(_CParams), i32, P]),
+        "mocd_server_step": (ctypes.c_int, [P, P, P, P]),
+        "mocd_server_job_state": (ctypes.c_int, [P, i64, P, P]),
+        "mocd_server_result": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, P]),
+        "mocd_server_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -263,6 +270,63 @@ def batch_destroy(b):
     if b is not None and b.value:
         load().mocd_batch_destroy(b)
         b.value = None
+
+
+class Server:
+    """Continuous-batching detection server (mocd_server_* in include/mocd.h)."""
+
+    QUEUED, RUNNING, DONE, FAILED = 0, 1, 2, 3
+
+    def __init__(self, hbm_budget_bytes: int, max_running: int = 64, depth: int = 2):
+        self.h = ctypes.c_void_p()
+        _check(load().mocd_server_create(ctypes.byref(self.h), int(hbm_budget_bytes), int(max_running),
+                                         int(depth)), "mocd_server_create")
+        self._n = {}
+        self._np = {}
+
+    def submit(self, row_ptr, col_idx, params: Params, generations: int = 100) -> int:
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+        c = params._c()
+        jid = ctypes.c_int64()
+        _check(load().mocd_server_submit(self.h, rp.size - 1, _p(rp), _p(ci), ctypes.byref(c), int(generations),
+                                         ctypes.byref(jid)), "mocd_server_submit")
+        self._n[jid.value] = rp.size - 1
+        self._np[jid.value] = params.pop_size
+        return jid.value
+
+    def step(self):
+        r = ctypes.c_int32()
+        q = ctypes.c_int32()
+        d = ctypes.c_int32()
+        _check(load().mocd_server_step(self.h, ctypes.byref(r), ctypes.byref(q), ctypes.byref(d)), "mocd_server_step")
+        return r.value, q.value, d.value
+
+    def state(self, job_id: int):
+        st = ctypes.c_int32()
+        status = ctypes.c_int32()
+        _check(load().mocd_server_job_state(self.h, int(job_id), ctypes.byref(st), ctypes.byref(status)),
+               "mocd_server_job_state")
+        return st.value, status.value
+
+    def result(self, job_id: int) -> Front:
+        n, cap = self._n[job_id], self._np[job_id]
+        count = ctypes.c_int32()
+        best = ctypes.c_int32()
+        labels = np.zeros((cap, n), dtype=np.int32)
+        f1 = np.zeros(cap)
+        f2 = np.zeros(cap)
+        intra = np.zeros(cap, dtype=np.int64)
+        sumsq = np.zeros(cap, dtype=np.int64)
+        _check(load().mocd_server_result(self.h, int(job_id), cap, ctypes.byref(count), _p(labels), _p(f1), _p(f2),
+                                         _p(intra), _p(sumsq), ctypes.byref(best)), "mocd_server_result")
+        k = count.value
+        return Front(labels[:k], f1[:k], f2[:k], intra[:k], sumsq[:k], best.value)
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            load().mocd_server_destroy(self.h)
+            self.h.value = None
 
 
 def synchronize(ctx):

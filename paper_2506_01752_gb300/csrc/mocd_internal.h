@@ -16,7 +16,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+struct mocd_ctx;
+
 namespace mocd {
+
+// Record `ev` on the context's stream (after all work issued so far).
+int record_on_stream(mocd_ctx *c, cudaEvent_t ev);
 
 constexpr int kMaxPop = 128;      // N_p limit: one int4 of labels per lane per row
 constexpr int kMaxParents = 16;   // E_S limit

@@ -371,6 +371,13 @@ int download_members(mocd_ctx *c, const int32_t *pos_host, int count, int32_t *l
 
 }  // namespace
 
+int mocd::record_on_stream(mocd_ctx *c, cudaEvent_t ev)
+{
+    if (!c || !ev) return MOCD_ERR_INVALID_ARG;
+    CK(cudaEventRecord(ev, c->stream));
+    return MOCD_OK;
+}
+
 extern "C" {
 
 const char *mocd_status_string(int status)

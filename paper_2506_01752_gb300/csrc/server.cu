@@ -1,0 +1,244 @@
+// server.cu -- continuous-batching detection server on top of the per-job
+// contexts of runtime.cu (see mocd_server_* in include/mocd.h).
+//
+// Every running job owns a context (graph, population buffers, stream and
+// per-generation CUDA graph). A scheduling round retires finished jobs,
+// admits queued ones within the device-memory budget and enqueues a few more
+// generation-graph launches for each running job on its own stream; the GPU
+// runs the jobs' kernels concurrently, and jobs enter and leave between
+// rounds without any re-capture.
+#include <cuda_runtime.h>
+
+#include <deque>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "mocd.h"
+#include "mocd_internal.h"
+
+namespace {
+
+enum { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3 };
+
+struct Job {
+    int64_t id = 0;
+    int state = kQueued;
+    int status = MOCD_OK;
+    int64_t n = 0;
+    std::vector<int64_t> row_ptr;
+    std::vector<int32_t> col_idx;
+    mocd_params params{};
+    int32_t generations = 0;
+    int32_t issued = 0;
+    int64_t footprint = 0;
+    mocd_ctx *ctx = nullptr;
+    cudaEvent_t done = nullptr;
+    // result
+    int32_t count = 0, best = -1;
+    std::vector<int32_t> labels;
+    std::vector<double> f1, f2;
+    std::vector<int64_t> intra, sumsq;
+};
+
+// Device bytes a job holds while it runs: four label buffers, the degree
+// histogram, the CSR, the node order and the small state.
+int64_t footprint(int64_t n, int64_t nnz, int32_t pop)
+{
+    const int64_t W = (pop + 3) & ~3;
+    return 4 * n * W * 4 + (int64_t)pop * n * 4 + (n + 1) * 4 + nnz * 4 + n * 4 + (1 << 16);
+}
+
+}  // namespace
+
+struct mocd_server {
+    int64_t budget = 0;
+    int64_t used = 0;
+    int32_t max_running = 1;
+    int32_t depth = 1;
+    int64_t next_id = 1;
+    int32_t done_count = 0;
+    std::deque<Job *> queue;
+    std::vector<Job *> running;
+    std::map<int64_t, Job *> jobs;
+};
+
+extern "C" {
+
+int mocd_server_create(mocd_server **out, int64_t hbm_budget_bytes, int32_t max_running, int32_t depth)
+{
+    if (!out) return MOCD_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (hbm_budget_bytes <= 0 || max_running < 1 || depth < 1) return MOCD_ERR_INVALID_ARG;
+    mocd_server *s = new (std::nothrow) mocd_server();
+    if (!s) return MOCD_ERR_OUT_OF_MEMORY;
+    s->budget = hbm_budget_bytes;
+    s->max_running = max_running;
+    s->depth = depth;
+    *out = s;
+    return MOCD_OK;
+}
+
+int mocd_server_submit(mocd_server *s, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                       const mocd_params *params, int32_t generations, int64_t *job_id)
+{
+    if (!s || !row_ptr || !params || !job_id || n < 1 || generations < 0) return MOCD_ERR_INVALID_ARG;
+    if (row_ptr[n] > 0 && !col_idx) return MOCD_ERR_INVALID_ARG;
+    Job *j = new (std::nothrow) Job();
+    if (!j) return MOCD_ERR_OUT_OF_MEMORY;
+    j->id = s->next_id++;
+    j->n = n;
+    j->row_ptr.assign(row_ptr, row_ptr + n + 1);
+    if (row_ptr[n] > 0) j->col_idx.assign(col_idx, col_idx + row_ptr[n]);
+    j->params = *params;
+    j->generations = generations;
+    j->footprint = footprint(n, row_ptr[n], params->pop_size);
+    s->queue.push_back(j);
+    s->jobs[j->id] = j;
+    *job_id = j->id;
+    return MOCD_OK;
+}
+
+static void release(mocd_server *s, Job *j)
+{
+    if (j->done) cudaEventDestroy(j->done);
+    j->done = nullptr;
+    if (j->ctx) {
+        mocd_destroy(j->ctx);
+        s->used -= j->footprint;
+    }
+    j->ctx = nullptr;
+}
+
+static void fail(mocd_server *s, Job *j, int status)
+{
+    release(s, j);
+    j->state = kFailed;
+    j->status = status;
+    s->done_count += 1;
+}
+
+int mocd_server_step(mocd_server *s, int32_t *running, int32_t *queued, int32_t *done)
+{
+    if (!s) return MOCD_ERR_INVALID_ARG;
+    // 1. Retire jobs whose last generation has completed.
+    for (size_t k = 0; k < s->running.size();) {
+        Job *j = s->running[k];
+        bool finished = false;
+        if (j->issued == j->generations) {
+            const cudaError_t q = cudaEventQuery(j->done);
+            if (q == cudaSuccess) finished = true;
+            else if (q != cudaErrorNotReady) {
+                fail(s, j, MOCD_ERR_CUDA);
+                s->running.erase(s->running.begin() + k);
+                continue;
+            }
+        }
+        if (!finished) {
+            ++k;
+            continue;
+        }
+        const int64_t cap = j->params.pop_size;
+        j->labels.resize((size_t)cap * (size_t)j->n);
+        j->f1.resize(cap);
+        j->f2.resize(cap);
+        j->intra.resize(cap);
+        j->sumsq.resize(cap);
+        const int rc = mocd_pareto_front(j->ctx, (int32_t)cap, &j->count, j->labels.data(), j->f1.data(),
+                                         j->f2.data(), j->intra.data(), j->sumsq.data(), &j->best);
+        if (rc) {
+            fail(s, j, rc);
+        } else {
+            j->labels.resize((size_t)j->count * (size_t)j->n);
+            release(s, j);
+            j->state = kDone;
+            s->done_count += 1;
+        }
+        s->running.erase(s->running.begin() + k);
+    }
+    // 2. Admit queued jobs in order while they fit.
+    while (!s->queue.empty() && (int32_t)s->running.size() < s->max_running) {
+        Job *j = s->queue.front();
+        if (j->footprint > s->budget) {
+            s->queue.pop_front();
+            fail(s, j, MOCD_ERR_OUT_OF_MEMORY);
+            continue;
+        }
+        if (s->used + j->footprint > s->budget) break;
+        s->queue.pop_front();
+        int rc = mocd_graph_upload(&j->ctx, j->n, j->row_ptr.data(), j->col_idx.data(), nullptr);
+        if (rc == MOCD_OK) {
+            s->used += j->footprint;
+            rc = mocd_population_init(j->ctx, &j->params);
+        }
+        if (rc == MOCD_OK && cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming) != cudaSuccess)
+            rc = MOCD_ERR_CUDA;
+        if (rc) {
+            fail(s, j, rc);
+            continue;
+        }
+        std::vector<int64_t>().swap(j->row_ptr);
+        std::vector<int32_t>().swap(j->col_idx);
+        j->state = kRunning;
+        s->running.push_back(j);
+    }
+    // 3. Enqueue more generations of every running job on its own stream.
+    for (Job *j : s->running) {
+        const int32_t k = j->generations - j->issued < s->depth ? j->generations - j->issued : s->depth;
+        if (k <= 0) continue;
+        int rc = mocd_generation(j->ctx, k);
+        j->issued += k;
+        // Completion marker after the job's last generation, on its own stream.
+        if (rc == MOCD_OK && j->issued == j->generations) rc = mocd::record_on_stream(j->ctx, j->done);
+        if (rc) j->issued = j->generations;  // surfaced as a failure at retirement via the event
+    }
+    if (running) *running = (int32_t)s->running.size();
+    if (queued) *queued = (int32_t)s->queue.size();
+    if (done) *done = s->done_count;
+    return MOCD_OK;
+}
+
+int mocd_server_job_state(mocd_server *s, int64_t job_id, int32_t *state, int32_t *status)
+{
+    if (!s || !state) return MOCD_ERR_INVALID_ARG;
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) return MOCD_ERR_INVALID_ARG;
+    *state = it->second->state;
+    if (status) *status = it->second->status;
+    return MOCD_OK;
+}
+
+int mocd_server_result(mocd_server *s, int64_t job_id, int32_t cap, int32_t *count, int32_t *labels,
+                       double *f1, double *f2, int64_t *intra, int64_t *sumsq, int32_t *best)
+{
+    if (!s || !count || cap < 0) return MOCD_ERR_INVALID_ARG;
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) return MOCD_ERR_INVALID_ARG;
+    Job *j = it->second;
+    if (j->state == kFailed) return j->status;
+    if (j->state != kDone) return MOCD_ERR_NOT_READY;
+    *count = j->count;
+    if (j->count > cap) return MOCD_ERR_BUFFER_TOO_SMALL;
+    for (int32_t k = 0; k < j->count; ++k) {
+        if (f1) f1[k] = j->f1[k];
+        if (f2) f2[k] = j->f2[k];
+        if (intra) intra[k] = j->intra[k];
+        if (sumsq) sumsq[k] = j->sumsq[k];
+    }
+    if (labels)
+        for (size_t k = 0; k < j->labels.size(); ++k) labels[k] = j->labels[k];
+    if (best) *best = j->best;
+    return MOCD_OK;
+}
+
+void mocd_server_destroy(mocd_server *s)
+{
+    if (!s) return;
+    for (auto &kv : s->jobs) {
+        release(s, kv.second);
+        delete kv.second;
+    }
+    delete s;
+}
+
+}  // extern "C"

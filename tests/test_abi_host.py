@@ -67,3 +67,21 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(mocd, "library_path", lambda: str(tmp_path / "absent.so"))
     with pytest.raises(ImportError):
         mocd.load()
+
+
+def test_server_host_side(lib):
+    """Queueing and job bookkeeping happen on the host only."""
+    srv = mocd.Server(1 << 30, max_running=2, depth=1)
+    try:
+        jid = srv.submit([0, 1, 2], [1, 0], mocd.Params(pop_size=4), 3)
+        assert jid == 1 and srv.state(jid) == (mocd.Server.QUEUED, 0)
+        with pytest.raises(mocd.MocdError) as e:
+            srv.result(jid)
+        assert e.value.status == -9
+        with pytest.raises(mocd.MocdError):
+            srv.state(99)
+    finally:
+        srv.close()
+    import ctypes
+    h = ctypes.c_void_p()
+    assert mocd.load().mocd_server_create(ctypes.byref(h), 0, 1, 1) == -1

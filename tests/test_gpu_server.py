@@ -1,0 +1,88 @@
+"""Continuous-batching server: each job's front equals the same job run alone
+(and the oracle's), whatever else is running, under a tight device-memory
+budget too."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2506_01752_gb300 as mocd
+import synth
+from _golden import graph, load
+
+pytestmark = pytest.mark.gpu
+
+
+def _jobs():
+    return [
+        (synth.workload("planted-1k", seed=0)[:2], dict(pop_size=100, seed=1), 12),
+        (synth.lfr_style(3000, 20, 50, 0.3, seed=2)[:2], dict(pop_size=64, seed=2), 8),
+        (graph(load("appE_operator_example.txt")), dict(pop_size=8, n_parents=3, seed=3), 6),
+        (synth.lfr_style(1500, 12, 60, 0.4, seed=4)[:2], dict(pop_size=100, seed=4), 10),
+        (graph(load("fig2_toy_graph.txt")), dict(pop_size=33, seed=5), 0),
+        (synth.planted_partition(6, 40, 0.3, 0.02, seed=6)[:2], dict(pop_size=50, seed=6), 15),
+    ]
+
+
+def _alone(rp, ci, kw, G):
+    h = mocd.graph_upload(rp, ci)
+    try:
+        mocd.population_init(h, mocd.Params(**kw))
+        mocd.generation(h, G)
+        return mocd.pareto_front(h)
+    finally:
+        mocd.destroy(h)
+
+
+def _drain(srv, ids, max_running):
+    for _ in range(100000):
+        running, queued, done = srv.step()
+        assert running <= max_running
+        if all(srv.state(j)[0] >= mocd.Server.DONE for j in ids):
+            return
+    raise AssertionError("server did not finish")
+
+
+@pytest.mark.parametrize("budget,max_running", [(1 << 34, 8), (6 << 20, 8), (1 << 34, 1)])
+def test_server_results_equal_alone(budget, max_running):
+    jobs = _jobs()
+    srv = mocd.Server(budget, max_running=max_running, depth=3)
+    try:
+        ids = [srv.submit(rp, ci, mocd.Params(**kw), G) for (rp, ci), kw, G in jobs]
+        assert srv.state(ids[0])[0] == mocd.Server.QUEUED
+        _drain(srv, ids, max_running)
+        for jid, ((rp, ci), kw, G) in zip(ids, jobs):
+            assert srv.state(jid) == (mocd.Server.DONE, 0)
+            got = srv.result(jid)
+            ref = _alone(rp, ci, kw, G)
+            assert got.best == ref.best
+            assert np.array_equal(got.labels, ref.labels)
+            assert np.array_equal(got.intra, ref.intra) and np.array_equal(got.sumsq, ref.sumsq)
+            assert np.array_equal(got.f1, ref.f1) and np.array_equal(got.f2, ref.f2)
+        # and the oracle agrees with one of them
+        (rp, ci), kw, G = jobs[1]
+        op = oracle.Params(**kw)
+        st = oracle.run(rp, ci, op, oracle.population_init(rp, ci, op), G)
+        members, best = oracle.pareto_front(st, int(rp[-1] // 2))
+        got = srv.result(ids[1])
+        assert got.best == best and np.array_equal(got.labels, st.labels[members])
+    finally:
+        srv.close()
+
+
+def test_server_failures():
+    srv = mocd.Server(1 << 20, max_running=4, depth=2)  # 1 MiB
+    try:
+        big_rp, big_ci, _ = synth.workload("planted-1k", seed=0)
+        j_big = srv.submit(big_rp, big_ci, mocd.Params(), 5)          # footprint > budget
+        j_bad = srv.submit([0, 1, 2], [0, 1], mocd.Params(pop_size=4), 5)  # self loops
+        rp, ci = graph(load("appE_operator_example.txt"))
+        j_ok = srv.submit(rp, ci, mocd.Params(pop_size=8), 5)
+        _drain(srv, [j_big, j_bad, j_ok], 4)
+        assert srv.state(j_big) == (mocd.Server.FAILED, -6)
+        assert srv.state(j_bad) == (mocd.Server.FAILED, -3)
+        assert srv.state(j_ok)[0] == mocd.Server.DONE
+        with pytest.raises(mocd.MocdError) as e:
+            srv.result(j_big)
+        assert e.value.status == -6
+    finally:
+        srv.close()
