@@ -50,6 +50,10 @@ def parse_args(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--requests", type=int, default=80, help="serving trace length (--workload serve)")
+    ap.add_argument("--hbm-budget-gb", type=int, default=64, help="server device-memory budget")
+    ap.add_argument("--max-running", type=int, default=8, help="server concurrency limit")
+    ap.add_argument("--policy", type=int, default=0, help="server admission: 0 FIFO, 1 shortest work first")
     ap.add_argument("--preroll-s", type=float, default=0.5,
                     help="seconds of extra untimed generations before timing (clock settling)")
     return ap.parse_args(argv)
@@ -508,12 +512,100 @@ def run_batch(args):
     return 0
 
 
+def run_serve(args):
+    """Poisson stream of detection requests (20/s, G = 100, graphs from
+    synth.serving_pool), served by the continuous-batching server and, for
+    comparison, by plain serial processing of the same trace (upload, init,
+    100 generations, front download, one request after another)."""
+    import torch
+    import paper_2506_01752_gb300 as mocd
+    import synth
+
+    torch.cuda.set_device(0)
+    mocd.build.build()
+    pool = synth.serving_pool(12, seed=0)
+    rng = np.random.default_rng(1)
+    n_req, rate, G = args.requests, 20.0, 100
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    picks = rng.integers(0, len(pool), n_req)
+    seeds = rng.integers(0, 1 << 31, n_req)
+    units = float(sum(100 * G * int(pool[k][0][-1] // 2) for k in picks))
+
+    def lat_stats(lat, makespan):
+        return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                "mean_s": float(np.mean(lat)), "makespan_s": makespan,
+                "edge_evals_per_s": units / makespan}
+
+    # warm up the library and the device
+    rp, ci, _ = pool[0]
+    h = mocd.graph_upload(rp, ci)
+    mocd.population_init(h, mocd.Params())
+    mocd.generation(h, 5)
+    mocd.pareto_front(h)
+    mocd.destroy(h)
+
+    # Continuous-batching server (background scheduler + admission workers).
+    srv = mocd.Server(args.hbm_budget_gb << 30, max_running=args.max_running, depth=8)
+    srv.start(admission_threads=2, policy=args.policy)
+    t0 = time.perf_counter()
+    ids, done_at, submitted = [], {}, 0
+    while len(done_at) < n_req:
+        now = time.perf_counter() - t0
+        while submitted < n_req and arrivals[submitted] <= now:
+            k = picks[submitted]
+            ids.append(srv.submit(pool[k][0], pool[k][1], mocd.Params(seed=int(seeds[submitted])), G))
+            submitted += 1
+        srv.step()
+        now = time.perf_counter() - t0
+        for i, jid in enumerate(ids):
+            if i not in done_at and srv.state(jid)[0] >= mocd.Server.DONE:
+                done_at[i] = now
+        time.sleep(0.0005)
+    srv_make = max(done_at.values())
+    srv_lat = np.array([done_at[i] - arrivals[i] for i in range(n_req)])
+    failed = sum(1 for j in ids if srv.state(j)[0] == mocd.Server.FAILED)
+    srv.close()
+
+    # Plain serial processing of the same trace.
+    t0 = time.perf_counter()
+    plain_lat = []
+    for i in range(n_req):
+        now = time.perf_counter() - t0
+        if arrivals[i] > now:
+            time.sleep(arrivals[i] - now)
+        k = picks[i]
+        h = mocd.graph_upload(pool[k][0], pool[k][1])
+        mocd.population_init(h, mocd.Params(seed=int(seeds[i])))
+        mocd.generation(h, G)
+        mocd.pareto_front(h)
+        mocd.destroy(h)
+        plain_lat.append(time.perf_counter() - t0 - arrivals[i])
+    plain_make = time.perf_counter() - t0
+
+    line = {
+        "metric": "detection request latency p50/p99 (s) and edge-evals/s [serving]",
+        "server": lat_stats(srv_lat, srv_make), "plain_serial": lat_stats(np.array(plain_lat), plain_make),
+        "failed": failed, "requests": n_req, "rate_per_s": rate, "generations": G,
+        "config": {"workload": "Poisson 20/s; LFR-style graphs, n log-spaced 1e3-1e6 (12-graph pool), "
+                               "mu U[0.1,0.6]; N_p=100, G=100",
+                   "hbm_budget_gb": args.hbm_budget_gb, "max_running": args.max_running, "depth": 8,
+                   "admission": "shortest work first" if args.policy else "first come first served",
+                   "admission_threads": 2,
+                   "pool": [d for _, _, d in pool]},
+        "n_gpus": 1, "dtype": "int32", "data": "synthetic",
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch64":
         return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_mine(args)
 
 

@@ -243,9 +243,18 @@ void mocd_batch_destroy(mocd_batch *b);
  *   mocd_server_job_state  *state: 0 queued, 1 running, 2 done, 3 failed
  *                       (*status then holds the MOCD_ERR_* code).
  *   mocd_server_result  as mocd_pareto_front, for a done job.
+ *   mocd_server_start   switches to background mode: a scheduler thread runs
+ *                       the rounds (mocd_server_step then only reports counts)
+ *                       and `admission_threads` workers (1..16) validate,
+ *                       upload and initialise admitted jobs while the GPU runs
+ *                       the others. policy 0 admits in submission order;
+ *                       policy 1 admits the queued job with the least work
+ *                       ((n + 2m) x (G + 1)) first.
+ * Calls on one server may come from any host thread.
  */
 typedef struct mocd_server mocd_server;
 int mocd_server_create(mocd_server **out, int64_t hbm_budget_bytes, int32_t max_running, int32_t depth);
+int mocd_server_start(mocd_server *s, int32_t admission_threads, int32_t policy);
 int mocd_server_submit(mocd_server *s, int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
                        const mocd_params *params, int32_t generations, int64_t *job_id);
 int mocd_server_step(mocd_server *s, int32_t *running, int32_t *queued, int32_t *done);

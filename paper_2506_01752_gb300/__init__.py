@@ -112,6 +112,7 @@ def load():
         "mocd_batch_destroy": (None, [P]),
         "mocd_server_create": (ctypes.c_int, [ctypes.POINTER(P), i64, i32, i32]),
         "mocd_server_submit": (ctypes.c_int, [P, i64, P, P, ctypes.POINTER(_CParams), i32, P]),
+        "mocd_server_start": (ctypes.c_int, [P, i32, i32]),
         "mocd_server_step": (ctypes.c_int, [P, P, P, P]),
         "mocd_server_job_state": (ctypes.c_int, [P, i64, P, P]),
         "mocd_server_result": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, P]),
@@ -283,6 +284,10 @@ class Server:
                                          int(depth)), "mocd_server_create")
         self._n = {}
         self._np = {}
+
+    def start(self, admission_threads: int = 2, policy: int = 0):
+        """Background mode: scheduler thread plus admission workers."""
+        _check(load().mocd_server_start(self.h, int(admission_threads), int(policy)), "mocd_server_start")
 
     def submit(self, row_ptr, col_idx, params: Params, generations: int = 100) -> int:
         rp = np.ascontiguousarray(row_ptr, dtype=np.int64)

@@ -87,15 +87,23 @@ int cuda_status(cudaError_t e)
         if (e_ != cudaSuccess) return cuda_status(e_);\
     } while (0)
 
+// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the
+// owner's stream): releasing one context never synchronises the device, so
+// other contexts (batch members, server jobs) keep running.
+void dev_free(void *p, cudaStream_t st)
+{
+    if (p) cudaFreeAsync(p, st);
+}
+
 template <class T>
-int grow(T **p, size_t *cap, size_t need)
+int grow(cudaStream_t st, T **p, size_t *cap, size_t need)
 {
     if (*p && *cap >= need) return MOCD_OK;
-    if (*p) cudaFree(*p);
+    dev_free(*p, st);
     *p = nullptr;
     *cap = 0;
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, std::max<size_t>(need, 1) * sizeof(T));
+    cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(need, 1) * sizeof(T), st);
     if (e != cudaSuccess) return cuda_status(e);
     *p = static_cast<T *>(q);
     *cap = need;
@@ -108,12 +116,12 @@ void free_population(mocd_ctx *c)
     if (c->graph) cudaGraphDestroy(c->graph);
     c->graph_exec = nullptr;
     c->graph = nullptr;
-    cudaFree(c->ps.buf[0]);
-    cudaFree(c->ps.buf[1]);
-    cudaFree(c->ps.q);
-    cudaFree(c->ps.c);
-    cudaFree(c->ps.hist);
-    cudaFree(c->d_small);
+    dev_free(c->ps.buf[0], c->stream);
+    dev_free(c->ps.buf[1], c->stream);
+    dev_free(c->ps.q, c->stream);
+    dev_free(c->ps.c, c->stream);
+    dev_free(c->ps.hist, c->stream);
+    dev_free(c->d_small, c->stream);
     c->ps = PopState{};
     c->d_small = nullptr;
     c->pop_cells = 0;
@@ -173,9 +181,9 @@ int prepare_population(mocd_ctx *c, const mocd_params *p)
         int32_t *b[4] = {};
         for (int k = 0; k < 4; ++k) {
             void *q = nullptr;
-            cudaError_t e = cudaMalloc(&q, cells * sizeof(int32_t));
+            cudaError_t e = cudaMallocAsync(&q, cells * sizeof(int32_t), c->stream);
             if (e != cudaSuccess) {
-                for (int j = 0; j < k; ++j) cudaFree(b[j]);
+                for (int j = 0; j < k; ++j) dev_free(b[j], c->stream);
                 return cuda_status(e);
             }
             b[k] = static_cast<int32_t *>(q);
@@ -198,7 +206,7 @@ int prepare_population(mocd_ctx *c, const mocd_params *p)
                              + sizeof(double) * 2 * kMaxPop               // fval
                              + 64;                                        // gen, alignment
         void *s = nullptr;
-        cudaError_t e = cudaMalloc(&s, bytes);
+        cudaError_t e = cudaMallocAsync(&s, bytes, c->stream);
         if (e != cudaSuccess) return cuda_status(e);
         c->d_small = s;
         char *q = static_cast<char *>(s);
@@ -220,7 +228,7 @@ int prepare_population(mocd_ctx *c, const mocd_params *p)
     }
     const size_t hist_need = (size_t)p->pop_size * (size_t)c->n;
     {
-        int rc = grow(&c->ps.hist, &c->hist_cap, hist_need);
+        int rc = grow(c->stream, &c->ps.hist, &c->hist_cap, hist_need);
         if (rc) return rc;
     }
     c->W = W;
@@ -339,11 +347,11 @@ int validate_labels(const mocd_ctx *c, const int32_t *labels, size_t count)
 int download_r(mocd_ctx *c, const int32_t *ridx, int count, int32_t *labels)
 {
     if (count <= 0 || !labels) return MOCD_OK;
-    int rc = grow(&c->d_im, &c->im_cap, (size_t)count * (size_t)c->n);
+    int rc = grow(c->stream, &c->d_im, &c->im_cap, (size_t)count * (size_t)c->n);
     if (rc) return rc;
     if (!c->d_idx) {
         void *q = nullptr;
-        CK(cudaMalloc(&q, sizeof(int32_t) * 2 * kMaxPop));
+        CK(cudaMallocAsync(&q, sizeof(int32_t) * 2 * kMaxPop, c->stream));
         c->d_idx = static_cast<int32_t *>(q);
     }
     CK(cudaMemcpyAsync(c->d_idx, ridx, sizeof(int32_t) * count, cudaMemcpyHostToDevice, c->stream));
@@ -455,10 +463,10 @@ int mocd_graph_upload(mocd_ctx **out, int64_t n, const int64_t *row_ptr, const i
     std::vector<int32_t> rp32(n + 1);
     for (int64_t v = 0; v <= n; ++v) rp32[v] = (int32_t)row_ptr[v];
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, sizeof(int32_t) * (n + 1));
+    cudaError_t e = cudaMallocAsync(&p, sizeof(int32_t) * (n + 1), c->stream);
     if (e != cudaSuccess) return fail(cuda_status(e));
     c->d_row_ptr = static_cast<int32_t *>(p);
-    e = cudaMalloc(&p, sizeof(int32_t) * nnz);
+    e = cudaMallocAsync(&p, sizeof(int32_t) * nnz, c->stream);
     if (e != cudaSuccess) return fail(cuda_status(e));
     c->d_col_idx = static_cast<int32_t *>(p);
     // Work order of the degree-proportional kernels: degree descending (ties
@@ -468,7 +476,7 @@ int mocd_graph_upload(mocd_ctx **out, int64_t n, const int64_t *row_ptr, const i
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
         return row_ptr[a + 1] - row_ptr[a] > row_ptr[b + 1] - row_ptr[b];
     });
-    e = cudaMalloc(&p, sizeof(int32_t) * n);
+    e = cudaMallocAsync(&p, sizeof(int32_t) * n, c->stream);
     if (e != cudaSuccess) return fail(cuda_status(e));
     c->d_order = static_cast<int32_t *>(p);
     if (cudaMemcpyAsync(c->d_order, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream) !=
@@ -506,7 +514,7 @@ int mocd_set_population(mocd_ctx *c, const mocd_params *params, const int32_t *l
     CK(cudaSetDevice(c->device));
     rc = prepare_population(c, params);
     if (rc) return rc;
-    rc = grow(&c->d_im, &c->im_cap, (size_t)params->pop_size * (size_t)c->n);
+    rc = grow(c->stream, &c->d_im, &c->im_cap, (size_t)params->pop_size * (size_t)c->n);
     if (rc) return rc;
     CK(cudaMemcpyAsync(c->d_im, labels, sizeof(int32_t) * (size_t)params->pop_size * (size_t)c->n,
                        cudaMemcpyHostToDevice, c->stream));
@@ -599,12 +607,12 @@ int mocd_evaluate(mocd_ctx *c, int32_t count, const int32_t *labels, int64_t *in
     CK(cudaSetDevice(c->device));
     const int batch = std::min<int>(count, kMaxPop);
     const size_t n = (size_t)c->n;
-    if ((rc = grow(&c->d_im, &c->im_cap, (size_t)batch * n))) return rc;
-    if ((rc = grow(&c->d_nm, &c->nm_cap, (size_t)kMaxPop * n))) return rc;
-    if ((rc = grow(&c->d_eval_hist, &c->eval_hist_cap, (size_t)batch * n))) return rc;
+    if ((rc = grow(c->stream, &c->d_im, &c->im_cap, (size_t)batch * n))) return rc;
+    if ((rc = grow(c->stream, &c->d_nm, &c->nm_cap, (size_t)kMaxPop * n))) return rc;
+    if ((rc = grow(c->stream, &c->d_eval_hist, &c->eval_hist_cap, (size_t)batch * n))) return rc;
     if (!c->d_eval_acc) {
         void *q = nullptr;
-        CK(cudaMalloc(&q, sizeof(unsigned long long) * 2 * kMaxPop));
+        CK(cudaMallocAsync(&q, sizeof(unsigned long long) * 2 * kMaxPop, c->stream));
         c->d_eval_acc = static_cast<unsigned long long *>(q);
     }
     const int grid = grid_for_eval(c->sms);
@@ -838,14 +846,15 @@ void mocd_destroy(mocd_ctx *c)
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_population(c);
-    cudaFree(c->d_row_ptr);
-    cudaFree(c->d_col_idx);
-    cudaFree(c->d_order);
-    cudaFree(c->d_im);
-    cudaFree(c->d_nm);
-    cudaFree(c->d_eval_acc);
-    cudaFree(c->d_idx);
-    cudaFree(c->d_eval_hist);
+    dev_free(c->d_row_ptr, c->stream);
+    dev_free(c->d_col_idx, c->stream);
+    dev_free(c->d_order, c->stream);
+    dev_free(c->d_im, c->stream);
+    dev_free(c->d_nm, c->stream);
+    dev_free(c->d_eval_acc, c->stream);
+    dev_free(c->d_idx, c->stream);
+    dev_free(c->d_eval_hist, c->stream);
+    if (c->stream) cudaStreamSynchronize(c->stream);
     for (int k = 0; k <= kStages; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

@@ -3,15 +3,23 @@
 //
 // Every running job owns a context (graph, population buffers, stream and
 // per-generation CUDA graph). A scheduling round retires finished jobs,
-// admits queued ones within the device-memory budget and enqueues a few more
+// admits queued ones within the device-memory budget and enqueues more
 // generation-graph launches for each running job on its own stream; the GPU
 // runs the jobs' kernels concurrently, and jobs enter and leave between
-// rounds without any re-capture.
+// rounds without any re-capture. In background mode (mocd_server_start) a
+// scheduler thread runs the rounds and admission workers do the host-side
+// graph validation, upload and initialisation of the next jobs while the GPU
+// is busy with the running ones.
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
 #include <deque>
 #include <map>
+#include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "mocd.h"
@@ -25,6 +33,7 @@ struct Job {
     int64_t id = 0;
     int state = kQueued;
     int status = MOCD_OK;
+    bool admitting = false;
     int64_t n = 0;
     std::vector<int64_t> row_ptr;
     std::vector<int32_t> col_idx;
@@ -32,6 +41,7 @@ struct Job {
     int32_t generations = 0;
     int32_t issued = 0;
     int64_t footprint = 0;
+    double work = 0.0;  // relative cost, for shortest-first admission
     mocd_ctx *ctx = nullptr;
     cudaEvent_t done = nullptr;
     // result
@@ -53,15 +63,180 @@ int64_t footprint(int64_t n, int64_t nnz, int32_t pop)
 
 struct mocd_server {
     int64_t budget = 0;
-    int64_t used = 0;
+    int64_t used = 0;  // footprint of admitting and running jobs
     int32_t max_running = 1;
     int32_t depth = 1;
+    int32_t policy = 0;  // 0: first come first served, 1: smallest work first
     int64_t next_id = 1;
     int32_t done_count = 0;
+    int device = 0;
     std::deque<Job *> queue;
-    std::vector<Job *> running;
+    std::vector<Job *> running;   // admitted (initialising or running)
     std::map<int64_t, Job *> jobs;
+    std::mutex mu;
+    std::condition_variable cv_admit;  // admission workers
+    std::vector<std::thread> threads;
+    std::atomic<bool> stop{false};
+    bool background = false;
+    std::deque<Job *> to_admit;
 };
+
+namespace {
+
+void release(mocd_server *s, Job *j)
+{
+    if (j->done) cudaEventDestroy(j->done);
+    j->done = nullptr;
+    if (j->ctx) mocd_destroy(j->ctx);
+    j->ctx = nullptr;
+}
+
+void finish(mocd_server *s, Job *j, int state, int status)
+{
+    release(s, j);
+    s->used -= j->footprint;
+    j->state = state;
+    j->status = status;
+    s->done_count += 1;
+}
+
+// Host-side admission work (validation, upload, initialisation); no lock held.
+int admit_job(Job *j)
+{
+    int rc = mocd_graph_upload(&j->ctx, j->n, j->row_ptr.data(), j->col_idx.data(), nullptr);
+    if (rc == MOCD_OK) rc = mocd_population_init(j->ctx, &j->params);
+    if (rc == MOCD_OK && cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming) != cudaSuccess)
+        rc = MOCD_ERR_CUDA;
+    std::vector<int64_t>().swap(j->row_ptr);
+    std::vector<int32_t>().swap(j->col_idx);
+    return rc;
+}
+
+// Next queued job to admit under the policy (front of the queue, or the
+// smallest piece of work).
+std::deque<Job *>::iterator pick(mocd_server *s)
+{
+    auto it = s->queue.begin();
+    if (s->policy == 1)
+        for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+            if ((*q)->work < (*it)->work) it = q;
+    return it;
+}
+
+// One scheduling round; the lock is held by the caller. In background mode
+// admitted jobs are handed to the workers instead of being initialised here.
+void round_locked(mocd_server *s, std::unique_lock<std::mutex> &lock)
+{
+    // 1. Retire jobs whose last generation has completed.
+    for (size_t k = 0; k < s->running.size();) {
+        Job *j = s->running[k];
+        if (j->admitting || j->issued < j->generations) {
+            ++k;
+            continue;
+        }
+        const cudaError_t q = cudaEventQuery(j->done);
+        if (q == cudaErrorNotReady) {
+            ++k;
+            continue;
+        }
+        if (q != cudaSuccess) {
+            finish(s, j, kFailed, MOCD_ERR_CUDA);
+        } else {
+            const int64_t cap = j->params.pop_size;
+            j->labels.resize((size_t)cap * (size_t)j->n);
+            j->f1.resize(cap);
+            j->f2.resize(cap);
+            j->intra.resize(cap);
+            j->sumsq.resize(cap);
+            const int rc = mocd_pareto_front(j->ctx, (int32_t)cap, &j->count, j->labels.data(), j->f1.data(),
+                                             j->f2.data(), j->intra.data(), j->sumsq.data(), &j->best);
+            if (rc == MOCD_OK) j->labels.resize((size_t)j->count * (size_t)j->n);
+            finish(s, j, rc == MOCD_OK ? kDone : kFailed, rc);
+        }
+        s->running.erase(s->running.begin() + k);
+    }
+    // 2. Admit queued jobs while they fit.
+    while (!s->queue.empty() && (int32_t)s->running.size() < s->max_running) {
+        auto it = pick(s);
+        Job *j = *it;
+        if (j->footprint > s->budget) {
+            s->queue.erase(it);
+            j->state = kFailed;
+            j->status = MOCD_ERR_OUT_OF_MEMORY;
+            s->done_count += 1;
+            continue;
+        }
+        if (s->used + j->footprint > s->budget) break;
+        s->queue.erase(it);
+        s->used += j->footprint;
+        j->admitting = true;
+        s->running.push_back(j);
+        if (s->background) {
+            s->to_admit.push_back(j);
+            s->cv_admit.notify_one();
+        } else {
+            lock.unlock();
+            const int rc = admit_job(j);
+            lock.lock();
+            j->admitting = false;
+            if (rc) {
+                for (size_t k = 0; k < s->running.size(); ++k)
+                    if (s->running[k] == j) s->running.erase(s->running.begin() + k);
+                finish(s, j, kFailed, rc);
+            } else {
+                j->state = kRunning;
+            }
+        }
+    }
+    // 3. Enqueue more generations of every running job on its own stream.
+    for (Job *j : s->running) {
+        if (j->admitting) continue;
+        const int32_t k = j->generations - j->issued < s->depth ? j->generations - j->issued : s->depth;
+        if (k <= 0) continue;
+        int rc = mocd_generation(j->ctx, k);
+        j->issued += k;
+        // Completion marker after the job's last generation, on its own stream.
+        if (rc == MOCD_OK && j->issued == j->generations) rc = mocd::record_on_stream(j->ctx, j->done);
+        if (rc) j->issued = j->generations;  // surfaced at retirement
+    }
+}
+
+void admission_worker(mocd_server *s)
+{
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lock(s->mu);
+    while (!s->stop) {
+        s->cv_admit.wait(lock, [&] { return s->stop || !s->to_admit.empty(); });
+        if (s->stop) break;
+        Job *j = s->to_admit.front();
+        s->to_admit.pop_front();
+        lock.unlock();
+        const int rc = admit_job(j);
+        lock.lock();
+        j->admitting = false;
+        if (rc) {
+            for (size_t k = 0; k < s->running.size(); ++k)
+                if (s->running[k] == j) s->running.erase(s->running.begin() + k);
+            finish(s, j, kFailed, rc);
+        } else {
+            j->state = kRunning;
+        }
+    }
+}
+
+void scheduler(mocd_server *s)
+{
+    cudaSetDevice(s->device);
+    while (!s->stop) {
+        {
+            std::unique_lock<std::mutex> lock(s->mu);
+            round_locked(s, lock);
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(100));
+    }
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -75,7 +250,26 @@ int mocd_server_create(mocd_server **out, int64_t hbm_budget_bytes, int32_t max_
     s->budget = hbm_budget_bytes;
     s->max_running = max_running;
     s->depth = depth;
+    if (cudaGetDevice(&s->device) != cudaSuccess) s->device = 0;
     *out = s;
+    return MOCD_OK;
+}
+
+int mocd_server_start(mocd_server *s, int32_t admission_threads, int32_t policy)
+{
+    if (!s || admission_threads < 1 || admission_threads > 16 || policy < 0 || policy > 1)
+        return MOCD_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lock(s->mu);
+    if (s->background) return MOCD_ERR_INVALID_ARG;
+    s->background = true;
+    s->policy = policy;
+    lock.unlock();
+    try {
+        for (int32_t k = 0; k < admission_threads; ++k) s->threads.emplace_back(admission_worker, s);
+        s->threads.emplace_back(scheduler, s);
+    } catch (...) {
+        return MOCD_ERR_OUT_OF_MEMORY;
+    }
     return MOCD_OK;
 }
 
@@ -86,112 +280,26 @@ int mocd_server_submit(mocd_server *s, int64_t n, const int64_t *row_ptr, const 
     if (row_ptr[n] > 0 && !col_idx) return MOCD_ERR_INVALID_ARG;
     Job *j = new (std::nothrow) Job();
     if (!j) return MOCD_ERR_OUT_OF_MEMORY;
-    j->id = s->next_id++;
     j->n = n;
     j->row_ptr.assign(row_ptr, row_ptr + n + 1);
     if (row_ptr[n] > 0) j->col_idx.assign(col_idx, col_idx + row_ptr[n]);
     j->params = *params;
     j->generations = generations;
     j->footprint = footprint(n, row_ptr[n], params->pop_size);
+    j->work = (double)(n + row_ptr[n]) * (double)(generations + 1);
+    std::lock_guard<std::mutex> lock(s->mu);
+    j->id = s->next_id++;
     s->queue.push_back(j);
     s->jobs[j->id] = j;
     *job_id = j->id;
     return MOCD_OK;
 }
 
-static void release(mocd_server *s, Job *j)
-{
-    if (j->done) cudaEventDestroy(j->done);
-    j->done = nullptr;
-    if (j->ctx) {
-        mocd_destroy(j->ctx);
-        s->used -= j->footprint;
-    }
-    j->ctx = nullptr;
-}
-
-static void fail(mocd_server *s, Job *j, int status)
-{
-    release(s, j);
-    j->state = kFailed;
-    j->status = status;
-    s->done_count += 1;
-}
-
 int mocd_server_step(mocd_server *s, int32_t *running, int32_t *queued, int32_t *done)
 {
     if (!s) return MOCD_ERR_INVALID_ARG;
-    // 1. Retire jobs whose last generation has completed.
-    for (size_t k = 0; k < s->running.size();) {
-        Job *j = s->running[k];
-        bool finished = false;
-        if (j->issued == j->generations) {
-            const cudaError_t q = cudaEventQuery(j->done);
-            if (q == cudaSuccess) finished = true;
-            else if (q != cudaErrorNotReady) {
-                fail(s, j, MOCD_ERR_CUDA);
-                s->running.erase(s->running.begin() + k);
-                continue;
-            }
-        }
-        if (!finished) {
-            ++k;
-            continue;
-        }
-        const int64_t cap = j->params.pop_size;
-        j->labels.resize((size_t)cap * (size_t)j->n);
-        j->f1.resize(cap);
-        j->f2.resize(cap);
-        j->intra.resize(cap);
-        j->sumsq.resize(cap);
-        const int rc = mocd_pareto_front(j->ctx, (int32_t)cap, &j->count, j->labels.data(), j->f1.data(),
-                                         j->f2.data(), j->intra.data(), j->sumsq.data(), &j->best);
-        if (rc) {
-            fail(s, j, rc);
-        } else {
-            j->labels.resize((size_t)j->count * (size_t)j->n);
-            release(s, j);
-            j->state = kDone;
-            s->done_count += 1;
-        }
-        s->running.erase(s->running.begin() + k);
-    }
-    // 2. Admit queued jobs in order while they fit.
-    while (!s->queue.empty() && (int32_t)s->running.size() < s->max_running) {
-        Job *j = s->queue.front();
-        if (j->footprint > s->budget) {
-            s->queue.pop_front();
-            fail(s, j, MOCD_ERR_OUT_OF_MEMORY);
-            continue;
-        }
-        if (s->used + j->footprint > s->budget) break;
-        s->queue.pop_front();
-        int rc = mocd_graph_upload(&j->ctx, j->n, j->row_ptr.data(), j->col_idx.data(), nullptr);
-        if (rc == MOCD_OK) {
-            s->used += j->footprint;
-            rc = mocd_population_init(j->ctx, &j->params);
-        }
-        if (rc == MOCD_OK && cudaEventCreateWithFlags(&j->done, cudaEventDisableTiming) != cudaSuccess)
-            rc = MOCD_ERR_CUDA;
-        if (rc) {
-            fail(s, j, rc);
-            continue;
-        }
-        std::vector<int64_t>().swap(j->row_ptr);
-        std::vector<int32_t>().swap(j->col_idx);
-        j->state = kRunning;
-        s->running.push_back(j);
-    }
-    // 3. Enqueue more generations of every running job on its own stream.
-    for (Job *j : s->running) {
-        const int32_t k = j->generations - j->issued < s->depth ? j->generations - j->issued : s->depth;
-        if (k <= 0) continue;
-        int rc = mocd_generation(j->ctx, k);
-        j->issued += k;
-        // Completion marker after the job's last generation, on its own stream.
-        if (rc == MOCD_OK && j->issued == j->generations) rc = mocd::record_on_stream(j->ctx, j->done);
-        if (rc) j->issued = j->generations;  // surfaced as a failure at retirement via the event
-    }
+    std::unique_lock<std::mutex> lock(s->mu);
+    if (!s->background) round_locked(s, lock);
     if (running) *running = (int32_t)s->running.size();
     if (queued) *queued = (int32_t)s->queue.size();
     if (done) *done = s->done_count;
@@ -201,6 +309,7 @@ int mocd_server_step(mocd_server *s, int32_t *running, int32_t *queued, int32_t 
 int mocd_server_job_state(mocd_server *s, int64_t job_id, int32_t *state, int32_t *status)
 {
     if (!s || !state) return MOCD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
     auto it = s->jobs.find(job_id);
     if (it == s->jobs.end()) return MOCD_ERR_INVALID_ARG;
     *state = it->second->state;
@@ -212,6 +321,7 @@ int mocd_server_result(mocd_server *s, int64_t job_id, int32_t cap, int32_t *cou
                        double *f1, double *f2, int64_t *intra, int64_t *sumsq, int32_t *best)
 {
     if (!s || !count || cap < 0) return MOCD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
     auto it = s->jobs.find(job_id);
     if (it == s->jobs.end()) return MOCD_ERR_INVALID_ARG;
     Job *j = it->second;
@@ -234,6 +344,12 @@ int mocd_server_result(mocd_server *s, int64_t job_id, int32_t cap, int32_t *cou
 void mocd_server_destroy(mocd_server *s)
 {
     if (!s) return;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->stop = true;
+    }
+    s->cv_admit.notify_all();
+    for (std::thread &t : s->threads) t.join();
     for (auto &kv : s->jobs) {
         release(s, kv.second);
         delete kv.second;

@@ -12,6 +12,7 @@ from .graphs import (  # noqa: F401
     lfr_style,
     random_labels,
     batch_instances,
+    serving_pool,
     workload,
     WORKLOADS,
 )

@@ -273,6 +273,21 @@ def batch_instances(count: int = 64, seed: int = 0):
     return out
 
 
+def serving_pool(count: int = 12, seed: int = 0, n_min: float = 1e3, n_max: float = 1e6):
+    """Graphs for a request stream: n log-spaced in [n_min, n_max], LFR-style
+    (average degree 16, maximum 200, communities 20-2000), mixing mu uniform
+    in [0.1, 0.6]. Returns a list of (row_ptr, col_idx, description)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        n = int(round(math.exp(math.log(n_min) + k * (math.log(n_max) - math.log(n_min)) / max(1, count - 1))))
+        mu = float(rng.uniform(0.1, 0.6))
+        rp, ci, _ = lfr_style(n, 16, 200 if n >= 20_000 else 50, mu, cmin=20,
+                              cmax=2000 if n >= 20_000 else 100, seed=int(rng.integers(0, 1 << 31)))
+        out.append((rp, ci, f"lfr n={n} mu={mu:.2f}"))
+    return out
+
+
 # Named workloads: shapes of the paper's experiments (Sec. 5.2, Table of
 # parameters: N_p = 100, G = 100, C_P = 0.8, M_P = 0.2, E_S = 4).
 WORKLOADS = {

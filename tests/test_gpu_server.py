@@ -34,21 +34,29 @@ def _alone(rp, ci, kw, G):
 
 
 def _drain(srv, ids, max_running):
-    for _ in range(100000):
+    import time
+    t_end = time.time() + 120
+    while time.time() < t_end:
         running, queued, done = srv.step()
         assert running <= max_running
         if all(srv.state(j)[0] >= mocd.Server.DONE for j in ids):
             return
+        time.sleep(0.0005)
     raise AssertionError("server did not finish")
 
 
-@pytest.mark.parametrize("budget,max_running", [(1 << 34, 8), (6 << 20, 8), (1 << 34, 1)])
-def test_server_results_equal_alone(budget, max_running):
+@pytest.mark.parametrize("budget,max_running,background", [
+    (1 << 34, 8, None), (6 << 20, 8, None), (1 << 34, 1, None),
+    (1 << 34, 8, 0), (6 << 20, 4, 1)])
+def test_server_results_equal_alone(budget, max_running, background):
     jobs = _jobs()
     srv = mocd.Server(budget, max_running=max_running, depth=3)
+    if background is not None:
+        srv.start(admission_threads=2, policy=background)
     try:
         ids = [srv.submit(rp, ci, mocd.Params(**kw), G) for (rp, ci), kw, G in jobs]
-        assert srv.state(ids[0])[0] == mocd.Server.QUEUED
+        if background is None:
+            assert srv.state(ids[0])[0] == mocd.Server.QUEUED
         _drain(srv, ids, max_running)
         for jid, ((rp, ci), kw, G) in zip(ids, jobs):
             assert srv.state(jid) == (mocd.Server.DONE, 0)
@@ -58,6 +66,8 @@ def test_server_results_equal_alone(budget, max_running):
             assert np.array_equal(got.labels, ref.labels)
             assert np.array_equal(got.intra, ref.intra) and np.array_equal(got.sumsq, ref.sumsq)
             assert np.array_equal(got.f1, ref.f1) and np.array_equal(got.f2, ref.f2)
+        if background is None:
+            assert srv.state(ids[0])[0] == mocd.Server.DONE
         # and the oracle agrees with one of them
         (rp, ci), kw, G = jobs[1]
         op = oracle.Params(**kw)
