@@ -53,32 +53,40 @@ struct SelShared {
     int keep[kMaxPop];
 };
 
-// Bitonic sort of one key per thread across the block (kSelThreads keys),
-// ascending; the compare-exchange is branch-free.
-__device__ __forceinline__ Key block_sort(SelShared &S, Key key)
+// Bitonic sort, ascending, of one key per thread over the first `size`
+// threads (a power of two, 32..kSelThreads); the other threads only join the
+// barriers. The compare-exchange is branch-free.
+__device__ __forceinline__ Key block_sort(SelShared &S, Key key, int size)
 {
     const int t = threadIdx.x;
+    const bool in = t < size;
 #pragma unroll 1
-    for (int k = 2; k <= kSelThreads; k <<= 1) {
+    for (int k = 2; k <= size; k <<= 1) {
 #pragma unroll 1
         for (int j = k >> 1; j > 0; j >>= 1) {
             Key other;
             if (j >= 32) {
-                S.sa[t] = key.a;
-                S.sb[t] = key.b;
+                if (in) {
+                    S.sa[t] = key.a;
+                    S.sb[t] = key.b;
+                }
                 __syncthreads();
-                other.a = S.sa[t ^ j];
-                other.b = S.sb[t ^ j];
+                if (in) {
+                    other.a = S.sa[t ^ j];
+                    other.b = S.sb[t ^ j];
+                }
                 __syncthreads();
-            } else {
+            } else if (in) {
                 other.a = __shfl_xor_sync(kFull, key.a, j);
                 other.b = __shfl_xor_sync(kFull, key.b, j);
             }
-            // Keep the smaller key where (t is the lower index) == (ascending run).
-            const bool want_min = ((t & j) == 0) == ((t & k) == 0);
-            const bool take = key_less(other, key) == want_min;
-            key.a = take ? other.a : key.a;
-            key.b = take ? other.b : key.b;
+            if (in) {
+                // Keep the smaller key where (t is the lower index) == (ascending run).
+                const bool want_min = ((t & j) == 0) == ((t & k) == 0);
+                const bool take = key_less(other, key) == want_min;
+                key.a = take ? other.a : key.a;
+                key.b = take ? other.b : key.b;
+            }
         }
     }
     return key;
@@ -119,67 +127,90 @@ __device__ int block_max_scan(SelShared &S, int v)
 
 // rank[], crowd[] and order[] of the first N points of S.k1 / S.k2 (N <= 256),
 // all indexed by point; ranks are 1-based. Same definitions as the textbook
-// O(N^2) procedure, computed with three block sorts and a few scans.
-__device__ void rank_crowd_order(SelShared &S, int N)
+// O(N^2) procedure, computed with block sorts and scans. With known_rank,
+// S.rank already holds every point's front (P's fronts are those R gave its
+// members) and only crowding and the order are computed.
+__device__ void rank_crowd_order(SelShared &S, int N, bool known_rank)
 {
     const int t = threadIdx.x;
     const bool valid = t < N;
+    int size = 32;
+    while (size < N) size <<= 1;
+    const bool in = t < size;
 
-    // (1) Sort by (k1, k2, index); invalid points go last. k1 < 2^31, so
-    // (k1 : hi32(k2), lo32(k2) : index) orders like the triple.
-    Key k;
-    {
-        const unsigned long long k1 = valid ? (unsigned long long)S.k1[t] : 0xffffffffull;
-        const unsigned long long k2 = valid ? (unsigned long long)S.k2[t] : kInf64;
-        k.a = (k1 << 32) | (k2 >> 32);
-        k.b = (k2 << 32) | (unsigned long long)t;
-    }
-    k = block_sort(S, k);
-    // Thread t now holds sorted position t.
-    const int id = (int)(k.b & 0xffffffffull);
-    const bool real = id < N;
-    const unsigned long long my1 = k.a >> 32;
-    const unsigned long long my2 = ((k.a & 0xffffffffull) << 32) | (k.b >> 32);
-    S.sa[t] = my1;
-    S.sb[t] = my2;
-    __syncthreads();
-    // Start of t's group of identical keys (identical points never dominate
-    // each other and share a front).
-    const bool head = t == 0 || S.sa[t - 1] != my1 || S.sb[t - 1] != my2;
-    const int gstart = block_max_scan(S, head ? t : 0);
-
-    // (2) Fronts. A remaining point is dominated iff some remaining point
-    // sorted before its group has k2 <= its k2.
-    bool rem = real;
-    int myrank = 0;
-    for (int r = 1;; ++r) {
-        const unsigned long long pm = block_min_scan(S, rem ? my2 : kInf64);
-        S.ia[t] = 0;
-        S.sa[t] = pm;
-        __syncthreads();
-        const unsigned long long before = gstart > 0 ? S.sa[gstart - 1] : kInf64;
-        const bool in = rem && before > my2;
-        if (in) {
-            myrank = r;
-            rem = false;
+    int e;  // point at position t of the fronts-contiguous (rank, k1, k2, index) order
+    if (!known_rank) {
+        // (1) Sort by (k1, k2, index); invalid points go last. k1 < 2^31, so
+        // (k1 : hi32(k2), lo32(k2) : index) orders like the triple.
+        Key k;
+        {
+            const unsigned long long k1 = valid ? (unsigned long long)S.k1[t] : 0xffffffffull;
+            const unsigned long long k2 = valid ? (unsigned long long)S.k2[t] : kInf64;
+            k.a = (k1 << 32) | (k2 >> 32);
+            k.b = (k2 << 32) | (unsigned long long)t;
         }
+        k = block_sort(S, k, size);
+        // Thread t now holds sorted position t.
+        const int id = (int)(k.b & 0xffffffffull);
+        const bool real = in && id < N;
+        const unsigned long long my1 = k.a >> 32;
+        const unsigned long long my2 = ((k.a & 0xffffffffull) << 32) | (k.b >> 32);
+        S.sa[t] = my1;
+        S.sb[t] = my2;
         __syncthreads();
-        if (!__syncthreads_or(rem)) break;
+        // Start of t's group of identical keys (identical points never
+        // dominate each other and share a front).
+        const bool head = t == 0 || S.sa[t - 1] != my1 || S.sb[t - 1] != my2;
+        const int gstart = block_max_scan(S, head ? t : 0);
+
+        // (2) Fronts. A remaining point is dominated iff some remaining point
+        // sorted before its group has k2 <= its k2.
+        bool rem = real;
+        int myrank = 0;
+        for (int r = 1;; ++r) {
+            const unsigned long long pm = block_min_scan(S, rem ? my2 : kInf64);
+            S.sa[t] = pm;
+            __syncthreads();
+            const unsigned long long before = gstart > 0 ? S.sa[gstart - 1] : kInf64;
+            const bool inf = rem && before > my2;
+            if (inf) {
+                myrank = r;
+                rem = false;
+            }
+            __syncthreads();
+            if (!__syncthreads_or(rem)) break;
+        }
+        if (real) S.rank[id] = myrank;
+        S.ia[t] = id;  // point at sorted position t
+        __syncthreads();
+
+        // (3) Fronts contiguous, each in (k1, index) order: sort by (rank, position).
+        Key f;
+        f.a = ((real ? (unsigned long long)myrank : 0xffffffffull) << 32) | (unsigned long long)t;
+        f.b = 0;
+        f = block_sort(S, f, size);
+        e = S.ia[(int)(f.a & 0xffffffffull)];
+    } else {
+        // Ranks known: one sort by (rank, k1, k2, index), packed as
+        // rank:9 | k1:31 | hi24(k2) and lo40(k2) | index:24.
+        Key f;
+        if (valid) {
+            const unsigned long long r = (unsigned long long)S.rank[t];
+            const unsigned long long k1 = (unsigned long long)S.k1[t];
+            const unsigned long long k2 = (unsigned long long)S.k2[t];
+            f.a = (r << 55) | (k1 << 24) | (k2 >> 40);
+            f.b = ((k2 & 0xffffffffffull) << 24) | (unsigned long long)t;
+        } else {
+            f.a = kInf64;
+            f.b = kInf64 - (unsigned long long)(kSelThreads - t);
+        }
+        f = block_sort(S, f, size);
+        e = (int)(f.b & 0xffffffull);
     }
-    if (real) S.rank[id] = myrank;
-    S.ia[t] = id;  // point at sorted position t
     for (int q = t; q <= kSelThreads; q += blockDim.x) S.fsize[q] = 0;
     __syncthreads();
-    if (real) atomicAdd(&S.fsize[myrank], 1);
-
-    // (3) Fronts contiguous, each in (k1, index) order: sort by (rank, position).
-    Key f;
-    f.a = ((real ? (unsigned long long)myrank : 0xffffffffull) << 32) | (unsigned long long)t;
-    f.b = 0;
-    f = block_sort(S, f);
-    const int posA = (int)(f.a & 0xffffffffull);
-    const int e = S.ia[posA];  // point at front-sorted position t
-    const bool ereal = e < N;
+    const bool ereal = in && e < N;
+    if (ereal) atomicAdd(&S.fsize[S.rank[e]], 1);
     const int er = ereal ? S.rank[e] : 0;
     const long long e1 = ereal ? S.k1[e] : 0, e2 = ereal ? S.k2[e] : 0;
     S.sa[t] = (unsigned long long)e1;
@@ -246,7 +277,7 @@ __device__ void rank_crowd_order(SelShared &S, int N)
         o.a = (r << 32) | (cb >> 32);
         o.b = (cb << 32) | (unsigned long long)t;
     }
-    o = block_sort(S, o);
+    o = block_sort(S, o, size);
     S.order[t] = (int)(o.b & 0xffffffffull);
     __syncthreads();
 }
@@ -282,18 +313,23 @@ select_kernel(GenParams gp, PopState ps, int mode)
             ps.rk[p] = S.k1[p];
             ps.rk[2 * kMaxPop + p] = S.k2[p];
         }
-        rank_crowd_order(S, 2 * np);
+        rank_crowd_order(S, 2 * np, false);
+        // The kept members keep their fronts: P is R's first fronts plus part
+        // of the next one, so every dominator of a member is kept too.
         long long n1 = 0, n2 = 0;
+        int nr = 0;
         if (p < np) {
             const int r = S.order[p];
             S.keep[p] = r;
             n1 = S.k1[r];
             n2 = S.k2[r];
+            nr = S.rank[r];
         }
         __syncthreads();
         if (p < np) {
             S.k1[p] = n1;
             S.k2[p] = n2;
+            S.rank[p] = nr;
         }
         __syncthreads();
     }
@@ -304,7 +340,7 @@ select_kernel(GenParams gp, PopState ps, int mode)
     }
 
     // Rank and crowding recomputed on P (Alg. 1, start of the generation).
-    rank_crowd_order(S, np);
+    rank_crowd_order(S, np, mode == 1);
     if (p < np) ps.prank[p] = S.rank[p];
 
     // TournamentSelection for generation gn = g + 1: parent j of child i is
