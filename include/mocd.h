@@ -63,7 +63,11 @@ typedef struct {
     double p_crossover;   /* C_P in [0, 1]: crossover iff u <= floor(C_P 2^32) */
     double p_mutation;    /* M_P in [0, 1]: node mutates iff u < floor(M_P 2^32) */
     uint64_t seed;        /* Philox4x32-10 key */
-    int32_t init_mode;    /* 0: labels uniform in [0, n) (Alg. 1 InitializePopulation) */
+    int32_t init_mode;    /* 0: labels uniform in [0, n) (Alg. 1 InitializePopulation);
+                             1: hybrid seeding: every node its own community,
+                             then one synchronous full-rate neighbour-majority
+                             step (the mutation rule of Sec. 4.3.2), ties broken
+                             by the INIT word of (node, individual) */
 } mocd_params;
 
 /*

@@ -53,6 +53,10 @@
  *     f2 = S/(4 m^2), each one division in double.
  *   - SelectSolution minimises 4 m (m - intra) + S (the same order as Q);
  *     the first member of the front in P order wins ties.
+ *   - Initialisation ("random hash-map partitions", "hybrid initialization"):
+ *     init_mode 0: label uniform in [0, n), pick(INIT word, n); init_mode 1:
+ *     every node starts as its own community (label v), then one synchronous
+ *     full-rate neighbour-majority sweep with the INIT word as tie-break.
  *   - Random stream layout (Philox4x32-10, key = (seed low, seed high)):
  *       per individual i and node v:   counter (v, i / 4, g, stage), word i % 4
  *         stage 1 INIT  (g = 0)  initial label pick(u, n)
@@ -442,19 +446,53 @@ static int check_params(const orc_params *pr)
     if (pr->pop_size < 1 || pr->n_parents < 1 || pr->n_parents > 64) return ORC_EINVAL;
     if (!(pr->p_crossover >= 0.0 && pr->p_crossover <= 1.0)) return ORC_EINVAL;
     if (!(pr->p_mutation >= 0.0 && pr->p_mutation <= 1.0)) return ORC_EINVAL;
-    if (pr->init_mode != 0) return ORC_EINVAL;
+    if (pr->init_mode != 0 && pr->init_mode != 1) return ORC_EINVAL;
     return ORC_OK;
 }
 
-/* InitializePopulation (Alg. 1): label of node v in individual i is
- * pick(INIT word, n), i.e. uniform in [0, n). P is [N_p][n]. */
+/* InitializePopulation (Alg. 1) for init_mode 0: label of node v in
+ * individual i is pick(INIT word, n), i.e. uniform in [0, n). P is [N_p][n]. */
 int orc_init_population(int64_t n, const orc_params *pr, int32_t *P)
 {
     int rc = check_params(pr);
     if (rc) return rc;
+    if (pr->init_mode != 0) return ORC_EINVAL;
     for (int32_t i = 0; i < pr->pop_size; ++i)
         for (int64_t v = 0; v < n; ++v)
             P[(int64_t)i * n + v] = (int32_t)orc_pick(draw_node(pr->seed, ST_INIT, 0, (uint32_t)i, (uint32_t)v), (uint32_t)n);
+    return ORC_OK;
+}
+
+/* init_mode 1: singletons (label v), then one synchronous neighbour-majority
+ * sweep of every node of positive degree (the mutation rule of Sec. 4.3.2 at
+ * rate 1), ties broken by the INIT word of (individual, node). */
+int orc_init_population_sweep(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                              const orc_params *pr, int32_t *P)
+{
+    int rc = check_params(pr);
+    if (rc) return rc;
+    int64_t dmax = 0;
+    for (int64_t v = 0; v < n; ++v)
+        if (row_ptr[v + 1] - row_ptr[v] > dmax) dmax = row_ptr[v + 1] - row_ptr[v];
+    int32_t *single = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *x = (int32_t *)malloc(sizeof(int32_t) * (size_t)(3 * dmax + 3));
+    if (!single || !x) { free(single); free(x); return ORC_ENOMEM; }
+    int32_t *s = x + dmax + 1, *ties = s + dmax + 1;
+    for (int64_t v = 0; v < n; ++v) single[v] = (int32_t)v;
+    for (int32_t i = 0; i < pr->pop_size; ++i) {
+        for (int64_t v = 0; v < n; ++v) {
+            int64_t d = row_ptr[v + 1] - row_ptr[v];
+            int32_t lab = single[v];
+            if (d > 0) {
+                for (int64_t e = 0; e < d; ++e) x[e] = single[col_idx[row_ptr[v] + e]];
+                int32_t t = mode_ties((int32_t)d, x, s, ties);
+                int32_t k = t > 1 ? (int32_t)orc_pick(draw_node(pr->seed, ST_INIT, 0, (uint32_t)i, (uint32_t)v), (uint32_t)t) : 0;
+                lab = ties[k];
+            }
+            P[(int64_t)i * n + v] = lab;
+        }
+    }
+    free(single); free(x);
     return ORC_OK;
 }
 
@@ -601,7 +639,8 @@ done:
 int orc_population_init(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
                         const orc_params *pr, int32_t *P, int64_t *k1, int64_t *k2)
 {
-    int rc = orc_init_population(n, pr, P);
+    int rc = pr->init_mode == 1 ? orc_init_population_sweep(n, row_ptr, col_idx, pr, P)
+                                : orc_init_population(n, pr, P);
     if (rc) return rc;
     int64_t m = row_ptr[n] / 2;
     for (int32_t i = 0; i < pr->pop_size; ++i) {

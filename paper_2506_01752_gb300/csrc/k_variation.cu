@@ -40,6 +40,44 @@ __global__ void init_population_kernel(int n, int W, int np, uint32_t k0, uint32
 }
 
 // ---------------------------------------------------------------------------
+// Hybrid initialisation (init_mode 1): every node starts as its own community
+// and then takes one synchronous neighbour-majority step at full rate, the tie
+// broken by the INIT word of (v, i). In a singleton partition the labels of
+// v's neighbours are their ids, all distinct because the uploaded adjacency
+// has no repeats, so every neighbour ties at count 1 and the tied labels in
+// ascending order are the adjacency row itself (it is stored sorted). The
+// step therefore reads entry pick(u, deg v) of the row; a node of degree 0
+// keeps label v.
+// ---------------------------------------------------------------------------
+__global__ void init_sweep_kernel(int n, int W, int np, uint32_t k0, uint32_t k1,
+                                  const int32_t *__restrict__ row_ptr,
+                                  const int32_t *__restrict__ col_idx, int32_t *__restrict__ dst)
+{
+    const int nq = W >> 2;
+    const long long total = (long long)n * nq;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int v = (int)(t / nq);
+        const int q = (int)(t % nq);
+        const int beg = __ldg(row_ptr + v);
+        const uint32_t d = (uint32_t)(__ldg(row_ptr + v + 1) - beg);
+        int4 o = make_int4(v, v, v, v);
+        if (d > 0) {
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)v, (uint32_t)q, 0u, kStageInit), k0, k1);
+            o.x = __ldg(col_idx + beg + pick_index(r.x, d));
+            o.y = __ldg(col_idx + beg + pick_index(r.y, d));
+            o.z = __ldg(col_idx + beg + pick_index(r.z, d));
+            o.w = __ldg(col_idx + beg + pick_index(r.w, d));
+        }
+        if (4 * q + 0 >= np) o.x = 0;
+        if (4 * q + 1 >= np) o.y = 0;
+        if (4 * q + 2 >= np) o.z = 0;
+        if (4 * q + 3 >= np) o.w = 0;
+        reinterpret_cast<int4 *>(dst)[t] = o;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Crossover. Row v of R = (P half | Q) is staged in shared memory; the next P
 // (environmental selection's keep list) is compacted into the other P half,
 // and child i of the generation gets
@@ -628,12 +666,17 @@ size_t crossover_smem()
 
 }  // namespace
 
-cudaError_t launch_init_population(const GenParams &gp, int32_t *dst, cudaStream_t s)
+cudaError_t launch_init_population(const GenParams &gp, int init_mode, const int32_t *row_ptr,
+                                   const int32_t *col_idx, int32_t *dst, cudaStream_t s)
 {
     const long long total = (long long)gp.n * (gp.W >> 2);
     long long blocks = (total + kBlock - 1) / kBlock;
     if (blocks > 65535LL * 16) blocks = 65535LL * 16;
-    init_population_kernel<<<(int)blocks, kBlock, 0, s>>>(gp.n, gp.W, gp.np, gp.key0, gp.key1, dst);
+    if (init_mode == 1)
+        init_sweep_kernel<<<(int)blocks, kBlock, 0, s>>>(gp.n, gp.W, gp.np, gp.key0, gp.key1, row_ptr,
+                                                         col_idx, dst);
+    else
+        init_population_kernel<<<(int)blocks, kBlock, 0, s>>>(gp.n, gp.W, gp.np, gp.key0, gp.key1, dst);
     return cudaGetLastError();
 }
 

@@ -67,7 +67,10 @@ struct GenParams {
 };
 
 // Launch wrappers (stream-ordered, return cudaGetLastError()).
-cudaError_t launch_init_population(const GenParams &gp, int32_t *dst, cudaStream_t s);
+// init_mode 0: labels uniform in [0, n); 1: singletons then one full-rate
+// neighbour-majority step (needs the sorted, repeat-free adjacency).
+cudaError_t launch_init_population(const GenParams &gp, int init_mode, const int32_t *row_ptr,
+                                   const int32_t *col_idx, int32_t *dst, cudaStream_t s);
 cudaError_t launch_crossover(const GenParams &gp, const PopState &ps, int grid, cudaStream_t s);
 // order: the nodes in the sequence the grid-stride loop visits them
 // (degree descending), or NULL for 0..n-1 (evaluation only).

@@ -143,7 +143,7 @@ int check_params(const mocd_ctx *c, const mocd_params *p)
     if (p->n_parents < 1 || p->n_parents > kMaxParents) return MOCD_ERR_INVALID_ARG;
     if (!(p->p_crossover >= 0.0 && p->p_crossover <= 1.0)) return MOCD_ERR_INVALID_ARG;
     if (!(p->p_mutation >= 0.0 && p->p_mutation <= 1.0)) return MOCD_ERR_INVALID_ARG;
-    if (p->init_mode != 0) return MOCD_ERR_INVALID_ARG;
+    if (p->init_mode != 0 && p->init_mode != 1) return MOCD_ERR_INVALID_ARG;
     if (c->dmax > 512) return MOCD_ERR_INVALID_ARG;  // mutation count table limit
     return MOCD_OK;
 }
@@ -500,7 +500,7 @@ int mocd_population_init(mocd_ctx *c, const mocd_params *params)
     CK(cudaSetDevice(c->device));
     rc = prepare_population(c, params);
     if (rc) return rc;
-    CK(launch_init_population(c->gp, c->ps.buf[1], c->stream));
+    CK(launch_init_population(c->gp, params->init_mode, c->d_row_ptr, c->d_col_idx, c->ps.buf[1], c->stream));
     return start_population(c, 0);
 }
 

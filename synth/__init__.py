@@ -5,6 +5,10 @@ seed. It holds none of the method's arithmetic: no objectives, no operators,
 no sorting and no random-number stream of the method. Both the CPU oracle
 (``oracle/``) and the CUDA path (``paper_2506_01752_gb300``) consume what it
 produces, and neither of them imports the other.
+
+``synth.quality`` scores a detected partition against the planted ground
+truth (NMI, AMI, pairwise F1); it is imported on its own and only by the tests
+and the benchmark.
 """
 from .graphs import (  # noqa: F401
     csr_from_edges,

@@ -117,10 +117,11 @@ def _compare_state(h, ref, m):
         assert fr.f1[a] == f1 and fr.f2[a] == f2
 
 
-@pytest.mark.parametrize("gname", ["fig2", "appE", "pair", "star", "planted-1k"])
-def test_init_matches_oracle(gname):
+@pytest.mark.parametrize("init_mode", [0, 1])
+@pytest.mark.parametrize("gname", ["fig2", "appE", "pair", "star", "planted-1k", "lfr-3k"])
+def test_init_matches_oracle(gname, init_mode):
     rp, ci = GRAPHS[gname]()
-    gp, op = _params(pop_size=37, seed=11)
+    gp, op = _params(pop_size=37, seed=11, init_mode=init_mode)
     with Ctx(rp, ci) as h:
         mocd.population_init(h, gp)
         _compare_state(h, oracle.population_init(rp, ci, op), int(rp[-1] // 2))
@@ -144,6 +145,10 @@ def test_init_matches_oracle(gname):
     ("pair", 3, dict(pop_size=100)),
     ("fig2", 5, dict(pop_size=127, n_parents=2)),
     ("fig2", 4, dict(pop_size=64, n_parents=7, p_mutation=0.5)),
+    # hybrid initialisation (singletons + one neighbour-majority step)
+    ("star", 3, dict(pop_size=24, init_mode=1)),
+    ("planted-1k", 4, dict(pop_size=100, init_mode=1)),
+    ("lfr-3k", 3, dict(pop_size=64, n_parents=4, seed=7, init_mode=1)),
 ])
 def test_generations_match_oracle(gname, G, kw):
     rp, ci = GRAPHS[gname]()

@@ -107,3 +107,51 @@ def test_offspring_labels_and_mutation_rate(oracle):
         for v in range(n):
             if deg[v]:
                 assert Q1[i, v] in set(st.labels[par[i, skip[i]]][ci[rp[v]:rp[v + 1]]].tolist())
+
+
+def _sweep_graph():
+    """Small graph with a hub, a path, isolated nodes and adjacency rows given
+    in shuffled order (the oracle may not rely on sorted rows)."""
+    rng = np.random.default_rng(17)
+    n = 60
+    u = list(rng.integers(0, 50, 120)) + [50] * 8 + [51, 52]
+    v = list(rng.integers(0, 50, 120)) + list(range(40, 48)) + [52, 53]
+    rp, ci = synth.csr_from_edges(n, u, v)  # nodes 54..59 isolated
+    for a in range(n):
+        seg = ci[rp[a]:rp[a + 1]].copy()
+        rng.shuffle(seg)
+        ci[rp[a]:rp[a + 1]] = seg
+    return rp, ci
+
+
+@pytest.mark.parametrize("seed", [0, 13, (1 << 40) + 5])
+def test_init_sweep_closed_form(oracle, seed):
+    """init_mode 1 = singletons, then one synchronous full-rate neighbour
+    majority step. Singleton labels are the node ids, all distinct, so every
+    neighbour of v ties at count 1 and the step takes the pick(u, deg v)-th
+    smallest neighbour id, u the INIT word of (v, i); degree 0 keeps v."""
+    rp, ci = _sweep_graph()
+    n = rp.size - 1
+    Np = 11
+    st = oracle.population_init(rp, ci, oracle.Params(pop_size=Np, seed=seed, init_mode=1))
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    for i in range(Np):
+        for v in range(n):
+            nb = sorted(ci[rp[v]:rp[v + 1]].tolist())
+            if not nb:
+                assert st.labels[i, v] == v
+                continue
+            u = int(oracle.philox((v, i // 4, 0, 1), key)[i % 4])
+            assert st.labels[i, v] == nb[(u * len(nb)) >> 32]
+    intra, S = oracle.objectives(rp, ci, st.labels)
+    m = int(rp[-1] // 2)
+    assert np.array_equal(st.k1, m - intra) and np.array_equal(st.k2, S)
+
+
+def test_init_sweep_two_node_path_and_isolated(oracle):
+    """0 - 1, 2 isolated: the synchronous step swaps the labels of 0 and 1
+    (each sees only the other's singleton label), node 2 keeps label 2."""
+    rp, ci = synth.csr_from_edges(3, [0], [1])
+    st = oracle.population_init(rp, ci, oracle.Params(pop_size=5, seed=2, init_mode=1))
+    assert np.array_equal(st.labels, np.tile([1, 0, 2], (5, 1)))
+    assert np.all(st.k1 == 1) and np.all(st.k2 == 2)  # intra 0; D = 1, 1
