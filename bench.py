@@ -9,6 +9,8 @@ N_p = 100, E_S = 4, C_P = 0.8, M_P = 0.2. The metric is N_p * m edge-evals per
 generation divided by the device time of the generation.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+    python bench.py --workload batch64|serve|quality   (batched jobs, serving,
+                                                        mixing sweep with NMI)
 
 Prints one JSON line. Under torchrun each rank runs an independent replica
 (a separate detection job with its own seed): weak scaling, no collective on
@@ -598,6 +600,61 @@ def run_serve(args):
     return 0
 
 
+def run_quality(args):
+    """The paper's mixing sweep at the benchmark size: for mu = 0.1 .. 0.7 and
+    each initialisation, one whole detection run (population init, G = 100
+    generations, Pareto front and Alg. 3's recommended member) on the LFR-style
+    n = 40,000 graph; run time on the device (CUDA events around init ..
+    front) and wall-clock from graph upload to the returned front, then the
+    recommended member scored against the planted communities."""
+    import torch
+    import paper_2506_01752_gb300 as mocd
+    import synth
+    from synth import quality
+
+    torch.cuda.set_device(0)
+    mocd.build.build()
+    stream = torch.cuda.Stream()
+    G = 100
+    rows = []
+    for mu in (0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7):
+        rp, ci, truth = synth.workload("lfr-40k", seed=args.seed, mu=mu)
+        m = int(rp[-1] // 2)
+        for init_mode in (0, 1):
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = mocd.graph_upload(rp, ci, stream)
+            try:
+                ev0.record(stream)
+                mocd.population_init(h, mocd.Params(seed=args.seed, init_mode=init_mode))
+                mocd.generation(h, G)
+                ev1.record(stream)
+                fr = mocd.pareto_front(h)
+                wall = time.perf_counter() - t0
+            finally:
+                mocd.destroy(h)
+            ev1.synchronize()
+            lab = fr.labels[fr.best]
+            rows.append({
+                "mu": mu, "init_mode": init_mode, "n": int(rp.size - 1), "m": m,
+                "device_ms": round(ev0.elapsed_time(ev1), 3), "wall_s": round(wall, 4),
+                "front": int(fr.f1.size), "modularity": round(1.0 - fr.f1[fr.best] - fr.f2[fr.best], 6),
+                "communities": int(np.unique(lab).size), "truth_communities": int(np.unique(truth).size),
+                "nmi": round(quality.nmi(lab, truth), 4), "ami": round(quality.ami(lab, truth), 4),
+                "f1": round(quality.pairwise_f1(lab, truth), 4),
+            })
+    line = {
+        "metric": "whole-run quality and run time (G = 100)", "unit": "NMI / ms",
+        "workload": "lfr-40k mixing sweep", "rows": rows, "n_gpus": 1, "dtype": "int32",
+        "data": "synthetic", "config": {"workload": "lfr-40k", "N_p": 100, "G": G, "E_S": 4,
+                                        "C_P": 0.8, "M_P": 0.2, "seed": args.seed},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -606,6 +663,8 @@ def main(argv=None):
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "quality":
+        return run_quality(args)
     return run_mine(args)
 
 

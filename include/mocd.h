@@ -119,6 +119,50 @@ int mocd_pareto_front(mocd_ctx *ctx, int32_t cap, int32_t *count, int32_t *label
                       int32_t *best);
 
 /*
+ * Community statistics of every member of the current Pareto front, in the
+ * order mocd_pareto_front lists them: the structural properties that Sec. 4.4
+ * names as alternative selection criteria and Alg. 3 leaves to the user.
+ * For a member with communities c (node sets V_c):
+ *   communities       host int64[cap] or NULL: number of non-empty communities k
+ *   size_sumsq        host int64[cap] or NULL: sum_c |V_c|^2 (mean size n / k,
+ *                     size variance size_sumsq / k - (n / k)^2)
+ *   mean_conductance  host double[cap] or NULL: (sum_c phi_c) / k with
+ *                     phi_c = cut_c / min(vol_c, 2m - vol_c) rounded once
+ *                     (one IEEE division; phi_c = 0 when cut_c = 0), cut_c the
+ *                     edges leaving V_c, vol_c the degree total of V_c; the sum
+ *                     is exact and rounded once to nearest, then divided by k
+ *   max_conductance   host double[cap] or NULL: max_c phi_c
+ * The results are exact functions of the labels (no dependence on launch
+ * order). Temporary device memory: 12 bytes per (member, node).
+ * Errors: INVALID_ARG, NOT_READY, BUFFER_TOO_SMALL (count set, nothing else
+ * written), OUT_OF_MEMORY, CUDA.
+ */
+int mocd_front_stats(mocd_ctx *ctx, int32_t cap, int32_t *count, int64_t *communities,
+                     int64_t *size_sumsq, double *mean_conductance,
+                     double *max_conductance);
+
+/* Selection criteria over the front (Alg. 3 and the alternatives of Sec. 4.4). */
+enum {
+    MOCD_SELECT_MODULARITY = 0,       /* largest Q = 1 - f1 - f2 (Alg. 3; Q is
+                                         Newman's modularity of the partition) */
+    MOCD_SELECT_COMMUNITIES = 1,      /* number of communities nearest `target` */
+    MOCD_SELECT_SIZE_VARIANCE = 2,    /* least variance of community sizes (exact) */
+    MOCD_SELECT_MEAN_CONDUCTANCE = 3, /* least mean conductance */
+    MOCD_SELECT_MAX_CONDUCTANCE = 4   /* least conductance of the worst community */
+};
+
+/*
+ * Index into the current front (mocd_pareto_front order) of the member that
+ * `criterion` prefers; ties go to the larger Q, then to the first in front
+ * order, so MOCD_SELECT_MODULARITY returns mocd_pareto_front's `best`.
+ *   target  the wanted number of communities (>= 1) for
+ *           MOCD_SELECT_COMMUNITIES, ignored otherwise
+ * Errors: INVALID_ARG (unknown criterion, target < 1 where it is used),
+ * NOT_READY, OUT_OF_MEMORY, CUDA.
+ */
+int mocd_select_solution(mocd_ctx *ctx, int32_t criterion, int64_t target, int32_t *index);
+
+/*
  * Copy out the whole current population P in P order (checkpoint; also the
  * state that environmental selection of Alg. 1 produced).
  *   labels   host int32[N_p * n] or NULL;  k1, k2 host int64[N_p] or NULL

@@ -68,6 +68,8 @@ def _load():
             "orc_population_init": (ctypes.c_int, [i64, P, P, P, P, P, P]),
             "orc_pareto_front": (ctypes.c_int, [i32, P, P, i64, P, P, P]),
             "orc_objective_values": (None, [i64, i64, i64, P, P]),
+            "orc_community_stats": (ctypes.c_int, [i64, P, P, i32, P, P, P, P, P]),
+            "orc_select_solution": (ctypes.c_int32, [i32, i64, i64, P, P, P, P, P, P, i32, i64]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -300,3 +302,28 @@ def pareto_front(state: State, m: int):
     _check(_load().orc_pareto_front(Np, _p(k1), _p(k2), m, ctypes.byref(count), _p(members),
                                     ctypes.byref(best)), "pareto_front")
     return members[: count.value].copy(), best.value
+
+
+def community_stats(row_ptr, col_idx, labels):
+    """Per labeling: (communities k, sum_c n_c^2, mean conductance, max
+    conductance), Sec. 4.4; see orc_community_stats."""
+    rp, ci = _graph(row_ptr, col_idx)
+    n = rp.size - 1
+    L = np.ascontiguousarray(np.atleast_2d(labels), dtype=np.int32)
+    cnt = L.shape[0]
+    k = np.zeros(cnt, np.int64)
+    sq = np.zeros(cnt, np.int64)
+    mean = np.zeros(cnt, np.float64)
+    mx = np.zeros(cnt, np.float64)
+    _check(_load().orc_community_stats(n, _p(rp), _p(ci), cnt, _p(L), _p(k), _p(sq), _p(mean), _p(mx)),
+           "community_stats")
+    return k, sq, mean, mx
+
+
+def select_solution(m: int, n: int, k1, k2, stats, criterion: int, target: int = 0) -> int:
+    """Index of the preferred front member (Alg. 3 / Sec. 4.4 criteria 0-4)."""
+    k1 = np.ascontiguousarray(k1, dtype=np.int64)
+    k2 = np.ascontiguousarray(k2, dtype=np.int64)
+    k, sq, mean, mx = (np.ascontiguousarray(a) for a in stats)
+    return int(_load().orc_select_solution(k1.size, m, n, _p(k1), _p(k2), _p(k), _p(sq), _p(mean), _p(mx),
+                                           criterion, target))

@@ -28,6 +28,9 @@
  *   env_select         Alg. 1, R = P u Q and EnvironmentalSelection(R, N_p).
  *   pareto_front       Alg. 1, F_1 = {p : rank(p) = 1}; Alg. 3 SelectSolution
  *                      with Q = 1 - f1 - f2 (Eq. selection).
+ *   community_stats    Sec. 4.4 alternative criteria: community count, size
+ *                      spread, conductance (definitions at the function).
+ *   select_solution    Alg. 3 and the Sec. 4.4 alternatives over a front.
  *
  * Readings where the paper is silent (each one a definition both sides follow):
  *   - E_S parents per crossover (Alg. 1 and the parameter table), chosen by E_S
@@ -685,4 +688,110 @@ void orc_objective_values(int64_t m, int64_t k1, int64_t k2, double *f1, double 
 {
     *f1 = (double)k1 / (double)m;
     *f2 = (double)k2 / (double)(4 * m * m);
+}
+
+/*
+ * Community statistics of `count` labelings (Sec. 4.4, the alternative
+ * criteria Alg. 3 leaves to the user). For labeling i and its communities
+ * V_c: k = number of non-empty communities; sumsq = sum_c |V_c|^2;
+ * phi_c = cut_c / min(vol_c, 2m - vol_c) as one IEEE division (0 if cut_c is
+ * 0), cut_c = edges with one endpoint in V_c, vol_c = sum of degrees in V_c;
+ * mean_phi = (exact sum_c phi_c, rounded once to nearest double) / k;
+ * max_phi = max_c phi_c. The exact sum: every phi_c is a double in
+ * [2^-30, 1] or 0, so phi_c * 2^88 is an integer below 2^89; those integers
+ * are added in 128 bits and the total converted once.
+ */
+int orc_community_stats(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, int32_t count,
+                        const int32_t *labels, int64_t *k_out, int64_t *sumsq_out,
+                        double *mean_phi, double *max_phi)
+{
+    int64_t *size = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    int64_t *vol = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    int64_t *cut = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    if (!size || !vol || !cut) { free(size); free(vol); free(cut); return ORC_ENOMEM; }
+    const int64_t two_m = row_ptr[n];
+    for (int32_t i = 0; i < count; ++i) {
+        const int32_t *L = labels + (int64_t)i * n;
+        memset(size, 0, sizeof(int64_t) * (size_t)n);
+        memset(vol, 0, sizeof(int64_t) * (size_t)n);
+        memset(cut, 0, sizeof(int64_t) * (size_t)n);
+        for (int64_t v = 0; v < n; ++v) {
+            if (L[v] < 0 || (int64_t)L[v] >= n) { free(size); free(vol); free(cut); return ORC_EINVAL; }
+            size[L[v]] += 1;
+            vol[L[v]] += row_ptr[v + 1] - row_ptr[v];
+            for (int64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e)
+                if (L[col_idx[e]] != L[v]) cut[L[v]] += 1;
+        }
+        int64_t k = 0, sq = 0;
+        unsigned __int128 sum = 0;
+        double mx = 0.0;
+        for (int64_t c = 0; c < n; ++c) {
+            if (!size[c]) continue;
+            k += 1;
+            sq += size[c] * size[c];
+            if (!cut[c]) continue;
+            const int64_t den = vol[c] < two_m - vol[c] ? vol[c] : two_m - vol[c];
+            const double phi = (double)cut[c] / (double)den;
+            if (phi > mx) mx = phi;
+            sum += (unsigned __int128)ldexp(phi, 88);
+        }
+        k_out[i] = k;
+        sumsq_out[i] = sq;
+        mean_phi[i] = ldexp((double)sum, -88) / (double)k;
+        max_phi[i] = mx;
+    }
+    free(size); free(vol); free(cut);
+    return ORC_OK;
+}
+
+/* Sign of var_a - var_b, var = (k sumsq - n^2) / k^2, exactly: integer parts
+ * of the two quotients first, then the remainders cross-multiplied (each
+ * remainder is below k^2 < 2^60, so the products fit in 128 bits). */
+static int variance_cmp(int64_t n, int64_t ka, int64_t sa, int64_t kb, int64_t sb)
+{
+    const unsigned __int128 n2 = (unsigned __int128)n * (unsigned __int128)n;
+    const unsigned __int128 na = (unsigned __int128)ka * (unsigned __int128)sa - n2;
+    const unsigned __int128 nb = (unsigned __int128)kb * (unsigned __int128)sb - n2;
+    const unsigned __int128 da = (unsigned __int128)ka * (unsigned __int128)ka;
+    const unsigned __int128 db = (unsigned __int128)kb * (unsigned __int128)kb;
+    const unsigned __int128 qa = na / da, qb = nb / db;
+    if (qa != qb) return qa < qb ? -1 : 1;
+    const unsigned __int128 ra = (na % da) * db, rb = (nb % db) * da;
+    return ra < rb ? -1 : ra > rb ? 1 : 0;
+}
+
+/*
+ * Index of the member a selection criterion prefers among `count` front
+ * members (Alg. 3 and the alternatives of Sec. 4.4): criterion 0 largest Q
+ * (the least 4 m k1 + k2), 1 number of communities nearest `target`, 2 least
+ * community-size variance, 3 least mean conductance, 4 least maximum
+ * conductance; ties go to the larger Q, then to the earlier member.
+ */
+int32_t orc_select_solution(int32_t count, int64_t m, int64_t n, const int64_t *k1, const int64_t *k2,
+                            const int64_t *k, const int64_t *sumsq, const double *mean_phi,
+                            const double *max_phi, int32_t criterion, int64_t target)
+{
+    int32_t best = -1;
+    for (int32_t a = 0; a < count; ++a) {
+        if (best < 0) { best = a; continue; }
+        const int32_t b = best;
+        int d = 0;
+        if (criterion == 1) {
+            const int64_t xa = k[a] > target ? k[a] - target : target - k[a];
+            const int64_t xb = k[b] > target ? k[b] - target : target - k[b];
+            d = xa < xb ? -1 : xa > xb ? 1 : 0;
+        } else if (criterion == 2) {
+            d = variance_cmp(n, k[a], sumsq[a], k[b], sumsq[b]);
+        } else if (criterion == 3) {
+            d = mean_phi[a] < mean_phi[b] ? -1 : mean_phi[a] > mean_phi[b] ? 1 : 0;
+        } else if (criterion == 4) {
+            d = max_phi[a] < max_phi[b] ? -1 : max_phi[a] > max_phi[b] ? 1 : 0;
+        }
+        if (d == 0) {
+            const int64_t Ka = 4 * m * k1[a] + k2[a], Kb = 4 * m * k1[b] + k2[b];
+            d = Ka < Kb ? -1 : 0;
+        }
+        if (d < 0) best = a;
+    }
+    return best;
 }

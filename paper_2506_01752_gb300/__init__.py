@@ -94,6 +94,8 @@ def load():
         "mocd_population_init": (ctypes.c_int, [P, ctypes.POINTER(_CParams)]),
         "mocd_generation": (ctypes.c_int, [P, i32]),
         "mocd_pareto_front": (ctypes.c_int, [P, i32, P, P, P, P, P, P, P]),
+        "mocd_front_stats": (ctypes.c_int, [P, i32, P, P, P, P, P]),
+        "mocd_select_solution": (ctypes.c_int, [P, i32, i64, P]),
         "mocd_get_population": (ctypes.c_int, [P, P, P, P, P]),
         "mocd_get_offspring": (ctypes.c_int, [P, P, P, P]),
         "mocd_set_population": (ctypes.c_int, [P, ctypes.POINTER(_CParams), P, i32]),
@@ -190,6 +192,43 @@ def pareto_front(ctx, with_labels: bool = True) -> Front:
                                     _p(sumsq), ctypes.byref(best)), "mocd_pareto_front")
     k = count.value
     return Front(labels[:k] if labels is not None else None, f1[:k], f2[:k], intra[:k], sumsq[:k], best.value)
+
+
+SELECT_MODULARITY = 0
+SELECT_COMMUNITIES = 1
+SELECT_SIZE_VARIANCE = 2
+SELECT_MEAN_CONDUCTANCE = 3
+SELECT_MAX_CONDUCTANCE = 4
+
+
+@dataclass
+class FrontStats:
+    """Community statistics of each front member, in pareto_front order."""
+    communities: np.ndarray       # int64: number of non-empty communities k
+    size_sumsq: np.ndarray        # int64: sum_c n_c^2
+    mean_conductance: np.ndarray  # float64: (exact sum_c phi_c, rounded once) / k
+    max_conductance: np.ndarray   # float64: max_c phi_c
+
+
+def front_stats(ctx) -> FrontStats:
+    cap = max(info(ctx)["pop_size"], 1)
+    count = ctypes.c_int32()
+    k = np.zeros(cap, np.int64)
+    sq = np.zeros(cap, np.int64)
+    mean = np.zeros(cap, np.float64)
+    mx = np.zeros(cap, np.float64)
+    _check(load().mocd_front_stats(ctx, cap, ctypes.byref(count), _p(k), _p(sq), _p(mean), _p(mx)),
+           "mocd_front_stats")
+    c = count.value
+    return FrontStats(k[:c], sq[:c], mean[:c], mx[:c])
+
+
+def select_solution(ctx, criterion: int = SELECT_MODULARITY, target: int = 0) -> int:
+    """Index into pareto_front of the member `criterion` prefers."""
+    idx = ctypes.c_int32()
+    _check(load().mocd_select_solution(ctx, int(criterion), int(target), ctypes.byref(idx)),
+           "mocd_select_solution")
+    return idx.value
 
 
 def get_population(ctx):

@@ -83,6 +83,15 @@ cudaError_t launch_evaluate(int n, int W, int count, const int32_t *row_ptr, con
 // environmental selection. Both then rank P and draw the next tournament.
 cudaError_t launch_select(const GenParams &gp, const PopState &ps, int mode, cudaStream_t s);
 cudaError_t launch_front(const GenParams &gp, const PopState &ps, cudaStream_t s);
+// Community statistics of the `count` front members (front_kernel's list):
+// rows [n][round4(count)] ints, volsize [count][n] u64 and cut [count][n] u32
+// zeroed, acc stats_acc_words() u64 zeroed; out [4][kMaxPop] u64 receives
+// communities, size_sumsq, mean conductance and max conductance (double bits).
+size_t stats_acc_words();
+cudaError_t launch_front_stats(const GenParams &gp, const PopState &ps, const int32_t *phalf, int count,
+                               const int32_t *row_ptr, const int32_t *col_idx, const int32_t *order,
+                               int32_t *rows, unsigned long long *volsize, uint32_t *cut,
+                               unsigned long long *acc, unsigned long long *out, int sms, cudaStream_t s);
 // out[k][v] = R_v[idx[k]] for k < count, R_v = (phalf row v | q row v); idx NULL: identity on phalf.
 cudaError_t launch_gather_individuals(int n, int W, int np, const int32_t *phalf, const int32_t *q,
                                       const int32_t *idx, int count, int32_t *out, cudaStream_t s);

@@ -67,6 +67,13 @@ struct mocd_ctx {
     uint32_t *d_eval_hist = nullptr;
     size_t eval_hist_cap = 0;
     int32_t *d_idx = nullptr;
+
+    // Scratch for mocd_front_stats.
+    unsigned long long *d_volsize = nullptr;  // [count][n]
+    size_t volsize_cap = 0;
+    uint32_t *d_cut = nullptr;                // [count][n]
+    size_t cut_cap = 0;
+    unsigned long long *d_stats = nullptr;    // acc words, then out [4][kMaxPop]
 };
 
 namespace {
@@ -377,6 +384,114 @@ int download_members(mocd_ctx *c, const int32_t *pos_host, int count, int32_t *l
     return download_r(c, ridx.data(), count, labels);
 }
 
+// F_1 as front_kernel lists it: fr = count, best, P positions; fint = intra
+// [kMaxPop] then S [kMaxPop] of each member.
+int read_front(mocd_ctx *c, std::vector<int32_t> &fr, std::vector<int64_t> &fint)
+{
+    const int np = c->gp.np;
+    CK(launch_front(c->gp, c->ps, c->stream));
+    fr.assign(2 + np, 0);
+    fint.assign(2 * kMaxPop, 0);
+    CK(cudaMemcpyAsync(fr.data(), c->ps.front, sizeof(int32_t) * (2 + np), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(fint.data(), c->ps.fint, sizeof(int64_t) * 2 * kMaxPop, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return MOCD_OK;
+}
+
+// Community statistics of the `count` members of the front that front_kernel
+// listed last; out = [4][kMaxPop] words (see launch_front_stats).
+int front_stats(mocd_ctx *c, int count, std::vector<unsigned long long> &out)
+{
+    const size_t n = (size_t)c->n;
+    const size_t Wf = (size_t)((count + 3) & ~3);
+    int rc;
+    if ((rc = grow(c->stream, &c->d_nm, &c->nm_cap, n * Wf))) return rc;
+    if ((rc = grow(c->stream, &c->d_volsize, &c->volsize_cap, n * (size_t)count))) return rc;
+    if ((rc = grow(c->stream, &c->d_cut, &c->cut_cap, n * (size_t)count))) return rc;
+    const size_t acc_words = stats_acc_words();
+    if (!c->d_stats) {
+        void *p = nullptr;
+        CK(cudaMallocAsync(&p, sizeof(unsigned long long) * (acc_words + 4 * kMaxPop), c->stream));
+        c->d_stats = static_cast<unsigned long long *>(p);
+    }
+    CK(cudaMemsetAsync(c->d_volsize, 0, sizeof(unsigned long long) * n * (size_t)count, c->stream));
+    CK(cudaMemsetAsync(c->d_cut, 0, sizeof(uint32_t) * n * (size_t)count, c->stream));
+    CK(cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * (acc_words + 4 * kMaxPop), c->stream));
+    const int32_t *phalf = c->ps.buf[(uint32_t)(c->host_gen + 1) & 1u];
+    CK(launch_front_stats(c->gp, c->ps, phalf, count, c->d_row_ptr, c->d_col_idx, c->d_order, c->d_nm,
+                          c->d_volsize, c->d_cut, c->d_stats, c->d_stats + acc_words, c->sms, c->stream));
+    out.assign(4 * kMaxPop, 0ull);
+    CK(cudaMemcpyAsync(out.data(), c->d_stats + acc_words, sizeof(unsigned long long) * 4 * kMaxPop,
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return MOCD_OK;
+}
+
+struct FrontMember {
+    int64_t K;            // 4 m (m - intra) + S: Alg. 3 order (smaller = larger Q)
+    int64_t communities;  // k
+    int64_t size_sumsq;   // sum_c n_c^2
+    double mean_phi, max_phi;
+};
+
+// a * b as three 64-bit limbs, most significant first.
+void mul_u128_u64(unsigned __int128 a, uint64_t b, uint64_t w[3])
+{
+    const unsigned __int128 lo = (unsigned __int128)(uint64_t)a * b;
+    const unsigned __int128 hi = (unsigned __int128)(uint64_t)(a >> 64) * b + (uint64_t)(lo >> 64);
+    w[2] = (uint64_t)lo;
+    w[1] = (uint64_t)hi;
+    w[0] = (uint64_t)(hi >> 64);
+}
+
+// Sign of var(a) - var(b), var = sum n_c^2 / k - (n / k)^2 = (k sumsq - n^2) / k^2,
+// compared exactly: (k_a sumsq_a - n^2) k_b^2 against (k_b sumsq_b - n^2) k_a^2.
+int compare_size_variance(const FrontMember &a, const FrontMember &b, int64_t n)
+{
+    const unsigned __int128 n2 = (unsigned __int128)n * (uint64_t)n;
+    const unsigned __int128 na = (unsigned __int128)(uint64_t)a.communities * (uint64_t)a.size_sumsq - n2;
+    const unsigned __int128 nb = (unsigned __int128)(uint64_t)b.communities * (uint64_t)b.size_sumsq - n2;
+    uint64_t x[3], y[3];
+    mul_u128_u64(na, (uint64_t)(b.communities * b.communities), x);
+    mul_u128_u64(nb, (uint64_t)(a.communities * a.communities), y);
+    for (int t = 0; t < 3; ++t)
+        if (x[t] != y[t]) return x[t] < y[t] ? -1 : 1;
+    return 0;
+}
+
+// Sign of (criterion of a) - (criterion of b); smaller is preferred.
+int compare_criterion(const FrontMember &a, const FrontMember &b, int criterion, int64_t target, int64_t n)
+{
+    switch (criterion) {
+    case MOCD_SELECT_COMMUNITIES: {
+        const int64_t da = a.communities > target ? a.communities - target : target - a.communities;
+        const int64_t db = b.communities > target ? b.communities - target : target - b.communities;
+        return da < db ? -1 : da > db ? 1 : 0;
+    }
+    case MOCD_SELECT_SIZE_VARIANCE: return compare_size_variance(a, b, n);
+    case MOCD_SELECT_MEAN_CONDUCTANCE: return a.mean_phi < b.mean_phi ? -1 : a.mean_phi > b.mean_phi ? 1 : 0;
+    case MOCD_SELECT_MAX_CONDUCTANCE: return a.max_phi < b.max_phi ? -1 : a.max_phi > b.max_phi ? 1 : 0;
+    default: return 0;
+    }
+}
+
+// The preferred member: least criterion, then least K (Alg. 3's order), then
+// the first in front order.
+int select_member(const std::vector<FrontMember> &mem, int criterion, int64_t target, int64_t n)
+{
+    int best = -1;
+    for (int k = 0; k < (int)mem.size(); ++k) {
+        if (best < 0) {
+            best = k;
+            continue;
+        }
+        int d = compare_criterion(mem[k], mem[best], criterion, target, n);
+        if (d == 0) d = mem[k].K < mem[best].K ? -1 : 0;
+        if (d < 0) best = k;
+    }
+    return best;
+}
+
 }  // namespace
 
 int mocd::record_on_stream(mocd_ctx *c, cudaEvent_t ev)
@@ -530,6 +645,61 @@ int mocd_generation(mocd_ctx *c, int32_t n_generations)
     for (int32_t k = 0; k < n_generations; ++k) CK(cudaGraphLaunch(c->graph_exec, c->stream));
     c->host_gen += n_generations;
     if (n_generations > 0 && c->timing) c->timing_valid = true;
+    return MOCD_OK;
+}
+
+int mocd_front_stats(mocd_ctx *c, int32_t cap, int32_t *count, int64_t *communities, int64_t *size_sumsq,
+                     double *mean_conductance, double *max_conductance)
+{
+    if (!c || !count || cap < 0) return MOCD_ERR_INVALID_ARG;
+    if (!c->ready) return MOCD_ERR_NOT_READY;
+    CK(cudaSetDevice(c->device));
+    std::vector<int32_t> fr;
+    std::vector<int64_t> fint;
+    int rc = read_front(c, fr, fint);
+    if (rc) return rc;
+    const int cnt = fr[0];
+    *count = cnt;
+    if (cnt > cap) return MOCD_ERR_BUFFER_TOO_SMALL;
+    std::vector<unsigned long long> out;
+    rc = front_stats(c, cnt, out);
+    if (rc) return rc;
+    for (int k = 0; k < cnt; ++k) {
+        if (communities) communities[k] = (int64_t)out[k];
+        if (size_sumsq) size_sumsq[k] = (int64_t)out[kMaxPop + k];
+        if (mean_conductance) std::memcpy(mean_conductance + k, &out[2 * kMaxPop + k], sizeof(double));
+        if (max_conductance) std::memcpy(max_conductance + k, &out[3 * kMaxPop + k], sizeof(double));
+    }
+    return MOCD_OK;
+}
+
+int mocd_select_solution(mocd_ctx *c, int32_t criterion, int64_t target, int32_t *index)
+{
+    if (!c || !index) return MOCD_ERR_INVALID_ARG;
+    if (criterion < MOCD_SELECT_MODULARITY || criterion > MOCD_SELECT_MAX_CONDUCTANCE) return MOCD_ERR_INVALID_ARG;
+    if (criterion == MOCD_SELECT_COMMUNITIES && target < 1) return MOCD_ERR_INVALID_ARG;
+    if (!c->ready) return MOCD_ERR_NOT_READY;
+    CK(cudaSetDevice(c->device));
+    std::vector<int32_t> fr;
+    std::vector<int64_t> fint;
+    int rc = read_front(c, fr, fint);
+    if (rc) return rc;
+    const int cnt = fr[0];
+    std::vector<unsigned long long> out(4 * kMaxPop, 0ull);
+    if (criterion != MOCD_SELECT_MODULARITY) {
+        rc = front_stats(c, cnt, out);
+        if (rc) return rc;
+    }
+    std::vector<FrontMember> mem(cnt);
+    for (int k = 0; k < cnt; ++k) {
+        FrontMember &f = mem[k];
+        f.K = 4 * c->m * (c->m - fint[k]) + fint[kMaxPop + k];
+        f.communities = (int64_t)out[k];
+        f.size_sumsq = (int64_t)out[kMaxPop + k];
+        std::memcpy(&f.mean_phi, &out[2 * kMaxPop + k], sizeof(double));
+        std::memcpy(&f.max_phi, &out[3 * kMaxPop + k], sizeof(double));
+    }
+    *index = select_member(mem, criterion, target, c->n);
     return MOCD_OK;
 }
 
@@ -854,6 +1024,9 @@ void mocd_destroy(mocd_ctx *c)
     dev_free(c->d_eval_acc, c->stream);
     dev_free(c->d_idx, c->stream);
     dev_free(c->d_eval_hist, c->stream);
+    dev_free(c->d_volsize, c->stream);
+    dev_free(c->d_cut, c->stream);
+    dev_free(c->d_stats, c->stream);
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (int k = 0; k <= kStages; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
