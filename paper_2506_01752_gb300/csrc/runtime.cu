@@ -6,11 +6,15 @@
 // Every kernel reads the generation number from device memory, so the same
 // graph is replayed for every generation with no host work in between.
 #include <algorithm>
+#include <atomic>
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "mocd.h"
@@ -349,6 +353,65 @@ int validate_labels(const mocd_ctx *c, const int32_t *labels, size_t count)
     return MOCD_OK;
 }
 
+// Runs f(v0, v1) on contiguous node ranges of about equal edge counts, on up
+// to 16 threads (inline when the graph is small).
+template <class F>
+void parallel_rows(const int64_t *row_ptr, int64_t n, F f)
+{
+    const int64_t nnz = row_ptr[n];
+    const unsigned hw = std::thread::hardware_concurrency();
+    int64_t T = std::min<int64_t>(std::min<int64_t>(hw ? hw : 1, 16), (nnz + n) / (1 << 16) + 1);
+    if (T <= 1) {
+        f(0, n);
+        return;
+    }
+    std::vector<int64_t> cut((size_t)T + 1);
+    cut[0] = 0;
+    cut[(size_t)T] = n;
+    for (int64_t t = 1; t < T; ++t)
+        cut[(size_t)t] = std::lower_bound(row_ptr, row_ptr + n, nnz * t / T) - row_ptr;
+    std::vector<std::thread> th;
+    th.reserve((size_t)T - 1);
+    for (int64_t t = 1; t < T; ++t) th.emplace_back(f, cut[(size_t)t], cut[(size_t)t + 1]);
+    f(cut[0], cut[1]);
+    for (auto &x : th) x.join();
+}
+
+// Writes one zero per 4 KiB of [p, p + bytes) from up to 16 threads: maps
+// every page of a buffer that is about to be overwritten.
+void prefault(void *p, size_t bytes)
+{
+    constexpr size_t kPage = 4096;
+    const size_t pages = bytes / kPage;
+    if (pages < 256) return;
+    volatile char *base = static_cast<volatile char *>(p);
+    const unsigned hw = std::thread::hardware_concurrency();
+    const size_t T = std::min<size_t>(std::min<size_t>(hw ? hw : 1, 16), pages / 256);
+    auto touch = [&](size_t a, size_t b) {
+        for (size_t k = a; k < b; ++k) base[k * kPage] = 0;
+    };
+    std::vector<std::thread> th;
+    for (size_t t = 1; t < T; ++t) th.emplace_back(touch, pages * t / T, pages * (t + 1) / T);
+    touch(0, pages / T);
+    for (auto &x : th) x.join();
+}
+
+// The status of the lowest-numbered failing row among concurrent checks.
+struct FirstError {
+    std::mutex mu;
+    int64_t row = INT64_MAX;
+    int code = MOCD_OK;
+    void record(int64_t v, int rc)
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (v < row) {
+            row = v;
+            code = rc;
+        }
+    }
+    int status() { return code; }
+};
+
 // Individual-major labels of `count` members of R = (P half, Q), given by
 // their R indices on the host.
 int download_r(mocd_ctx *c, const int32_t *ridx, int count, int32_t *labels)
@@ -365,6 +428,9 @@ int download_r(mocd_ctx *c, const int32_t *ridx, int count, int32_t *labels)
     const int32_t *phalf = c->ps.buf[(uint32_t)(c->host_gen + 1) & 1u];
     CK(launch_gather_individuals((int)c->n, c->W, c->gp.np, phalf, c->ps.q, c->d_idx, count, c->d_im,
                                  c->stream));
+    // While the gather runs: map the caller's (possibly freshly allocated)
+    // pages on several threads, so the copy does not fault page by page.
+    prefault(labels, sizeof(int32_t) * (size_t)count * (size_t)c->n);
     CK(cudaMemcpyAsync(labels, c->d_im, sizeof(int32_t) * (size_t)count * (size_t)c->n,
                        cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -533,26 +599,58 @@ int mocd_graph_upload(mocd_ctx **out, int64_t n, const int64_t *row_ptr, const i
     const int64_t nnz = row_ptr[n];
     if (nnz >= (int64_t(1) << 31)) return MOCD_ERR_INVALID_ARG;
     if (nnz > 0 && !col_idx) return MOCD_ERR_INVALID_ARG;
-    // Sorted copy of every adjacency list: self loops, repeats, symmetry.
-    std::vector<int32_t> adj(col_idx, col_idx + nnz);
+    // Rows that are already strictly increasing are used as given; otherwise
+    // a sorted copy of the adjacency is made. Then per row (in sorted order):
+    // range, self loop, repeat; then symmetry. The first failing row decides
+    // the status, as a sequential scan would.
+    std::atomic<bool> all_increasing{true};
+    parallel_rows(row_ptr, n, [&](int64_t v0, int64_t v1) {
+        for (int64_t v = v0; v < v1 && all_increasing.load(std::memory_order_relaxed); ++v)
+            for (int64_t k = row_ptr[v] + 1; k < row_ptr[v + 1]; ++k)
+                if (col_idx[k] <= col_idx[k - 1]) {
+                    all_increasing.store(false, std::memory_order_relaxed);
+                    break;
+                }
+    });
+    std::vector<int32_t> adj;
+    const int32_t *src = col_idx;
+    if (!all_increasing.load()) {
+        adj.assign(col_idx, col_idx + nnz);
+        parallel_rows(row_ptr, n, [&](int64_t v0, int64_t v1) {
+            for (int64_t v = v0; v < v1; ++v) std::sort(adj.data() + row_ptr[v], adj.data() + row_ptr[v + 1]);
+        });
+        src = adj.data();
+    }
+    FirstError err;
+    parallel_rows(row_ptr, n, [&](int64_t v0, int64_t v1) {
+        for (int64_t v = v0; v < v1; ++v) {
+            const int32_t *b = src + row_ptr[v], *e = src + row_ptr[v + 1];
+            for (const int32_t *q = b; q < e; ++q) {
+                int rc = MOCD_OK;
+                if (*q < 0 || *q >= n) rc = MOCD_ERR_INVALID_ARG;
+                else if (*q == v) rc = MOCD_ERR_SELF_LOOP;
+                else if (q > b && q[-1] == *q) rc = MOCD_ERR_DUPLICATE_EDGE;
+                if (rc) {
+                    err.record(v, rc);
+                    return;
+                }
+            }
+        }
+    });
+    if (err.status()) return err.status();
+    parallel_rows(row_ptr, n, [&](int64_t v0, int64_t v1) {
+        for (int64_t v = v0; v < v1; ++v)
+            for (int64_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
+                const int32_t u = src[k];
+                if (!std::binary_search(src + row_ptr[u], src + row_ptr[u + 1], (int32_t)v)) {
+                    err.record(v, MOCD_ERR_NOT_SYMMETRIC);
+                    return;
+                }
+            }
+    });
+    if (err.status()) return err.status();
     int dmax = 0;
-    for (int64_t v = 0; v < n; ++v) {
-        int32_t *b = adj.data() + row_ptr[v], *e = adj.data() + row_ptr[v + 1];
-        std::sort(b, e);
-        dmax = std::max<int>(dmax, (int)(e - b));
-        for (int32_t *p = b; p < e; ++p) {
-            if (*p < 0 || *p >= n) return MOCD_ERR_INVALID_ARG;
-            if (*p == v) return MOCD_ERR_SELF_LOOP;
-            if (p > b && p[-1] == *p) return MOCD_ERR_DUPLICATE_EDGE;
-        }
-    }
-    for (int64_t v = 0; v < n; ++v) {
-        for (int64_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
-            const int32_t u = adj[k];
-            if (!std::binary_search(adj.data() + row_ptr[u], adj.data() + row_ptr[u + 1], (int32_t)v))
-                return MOCD_ERR_NOT_SYMMETRIC;
-        }
-    }
+    for (int64_t v = 0; v < n; ++v) dmax = std::max<int>(dmax, (int)(row_ptr[v + 1] - row_ptr[v]));
     if (nnz == 0) return MOCD_ERR_EMPTY_GRAPH;
 
     mocd_ctx *c = new (std::nothrow) mocd_ctx();
@@ -585,12 +683,15 @@ int mocd_graph_upload(mocd_ctx **out, int64_t n, const int64_t *row_ptr, const i
     if (e != cudaSuccess) return fail(cuda_status(e));
     c->d_col_idx = static_cast<int32_t *>(p);
     // Work order of the degree-proportional kernels: degree descending (ties
-    // by node id), so that the costliest nodes are spread over all warps.
+    // by node id), so that the costliest nodes are spread over all warps. A
+    // counting sort on the degree.
     std::vector<int32_t> order(n);
-    for (int64_t v = 0; v < n; ++v) order[v] = (int32_t)v;
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-        return row_ptr[a + 1] - row_ptr[a] > row_ptr[b + 1] - row_ptr[b];
-    });
+    {
+        std::vector<int64_t> at((size_t)dmax + 2, 0);
+        for (int64_t v = 0; v < n; ++v) at[(size_t)(dmax - (row_ptr[v + 1] - row_ptr[v])) + 1] += 1;
+        for (size_t d = 1; d < at.size(); ++d) at[d] += at[d - 1];
+        for (int64_t v = 0; v < n; ++v) order[at[(size_t)(dmax - (row_ptr[v + 1] - row_ptr[v]))]++] = (int32_t)v;
+    }
     e = cudaMallocAsync(&p, sizeof(int32_t) * n, c->stream);
     if (e != cudaSuccess) return fail(cuda_status(e));
     c->d_order = static_cast<int32_t *>(p);
@@ -599,7 +700,7 @@ int mocd_graph_upload(mocd_ctx **out, int64_t n, const int64_t *row_ptr, const i
         return fail(MOCD_ERR_CUDA);
     if (cudaMemcpyAsync(c->d_row_ptr, rp32.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice,
                         c->stream) != cudaSuccess ||
-        cudaMemcpyAsync(c->d_col_idx, adj.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice,
+        cudaMemcpyAsync(c->d_col_idx, src, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice,
                         c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess)
         return fail(MOCD_ERR_CUDA);

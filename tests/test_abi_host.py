@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import paper_2506_01752_gb300 as mocd
+import synth
 from paper_2506_01752_gb300 import build as cuda_build
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "mocd.h")
@@ -85,3 +86,54 @@ def test_server_host_side(lib):
     import ctypes
     h = ctypes.c_void_p()
     assert mocd.load().mocd_server_create(ctypes.byref(h), 0, 1, 1) == -1
+
+
+def _big_graph():
+    rp, ci, _ = synth.lfr_style(20000, 20, 50, 0.3, seed=4)  # ~400k entries: several threads
+    return rp.astype(np.int64), ci.astype(np.int32).copy()
+
+
+def _validation_codes():
+    return {-1, -2, -3, -4, -5}
+
+
+def test_large_graph_validation_passes_with_shuffled_rows(lib):
+    """Rows in any order are accepted (a sorted copy is made); sorted rows are
+    used as given. Without a GPU the call then fails at the device step, not
+    in validation."""
+    rp, ci = _big_graph()
+    assert _upload_status(rp, ci) not in _validation_codes()
+    rng = np.random.default_rng(0)
+    for v in range(0, rp.size - 1, 7):
+        seg = ci[rp[v]:rp[v + 1]].copy()
+        rng.shuffle(seg)
+        ci[rp[v]:rp[v + 1]] = seg
+    assert _upload_status(rp, ci) not in _validation_codes()
+
+
+@pytest.mark.parametrize("defect", ["self_loop_first", "range_first", "asym", "dup_unsorted"])
+def test_large_graph_first_failing_row_decides(lib, defect):
+    """Defects in rows handled by different threads: the status is that of
+    the lowest-numbered failing row, as in a sequential scan; symmetry is
+    checked only after every row passed the per-row checks."""
+    rp, ci = _big_graph()
+    lo, hi = 10, rp.size - 50  # first and last thread ranges
+    if defect == "self_loop_first":
+        ci[rp[lo]] = lo           # row lo: self loop (also breaks symmetry)
+        ci[rp[hi]] = rp.size + 5  # row hi: out of range
+        want = -3
+    elif defect == "range_first":
+        ci[rp[lo]] = -7
+        ci[rp[hi]] = hi
+        want = -1
+    elif defect == "asym":
+        row = ci[rp[hi]:rp[hi + 1]]
+        w = int(np.setdiff1d(np.arange(rp.size - 1), np.concatenate([row, [hi]]))[0])
+        ci[rp[hi]] = w            # hi -> w without w -> hi (and u -> hi without hi -> u)
+        want = -2
+    else:
+        seg = ci[rp[hi]:rp[hi + 1]].copy()
+        seg[-1] = seg[0]           # repeated neighbour
+        ci[rp[hi]:rp[hi + 1]] = seg[::-1]
+        want = -4
+    assert _upload_status(rp, ci) == want
