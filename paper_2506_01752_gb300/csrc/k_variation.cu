@@ -404,8 +404,8 @@ __device__ __forceinline__ int warp_mode(const GenParams &gp, const int32_t *__r
         const bool in = e0 + lane < deg;
         int x = (int)(0x80000000u | lane);
         if (in)
-            x = deg <= kTileRows ? tile_col[(e0 + lane) * kTileStride]
-                                 : child[(size_t)__ldg(col_idx + beg + e0 + lane) * W + i];
+            x = e0 + lane < kTileRows ? tile_col[(e0 + lane) * kTileStride]
+                                      : child[(size_t)__ldg(col_idx + beg + e0 + lane) * W + i];
         // One insert per distinct label of the chunk, with its multiplicity.
         const unsigned peers = __match_any_sync(kFull, x);
         if (in && (peers & ((1u << lane) - 1u)) == 0) {
@@ -588,8 +588,18 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                     }
                 }
                 if (deg > kTileRows) {
-                    for (int e0 = 0; e0 < deg; e0 += 32) {
-                        const int my_u = e0 == 0 ? my_u0 : (e0 + lane < deg ? __ldg(col_idx + beg + e0 + lane) : 0);
+                    // The first kTileRows labels are still in the tile.
+                    if (has) {
+#pragma unroll 4
+                        for (int j = 0; j < kTileRows; ++j) {
+                            const int x = tile[j * kTileStride + lane];
+                            h0 += v0 && x == c0;
+                            h1 += v1 && x == c1;
+                            h2 += v2 && x == c2;
+                        }
+                    }
+                    for (int e0 = kTileRows; e0 < deg; e0 += 32) {
+                        const int my_u = e0 + lane < deg ? __ldg(col_idx + beg + e0 + lane) : 0;
                         const int cnt = min(32, deg - e0);
                         for (int j0 = 0; j0 < cnt; j0 += 8) {
                             int xs[8];
@@ -633,14 +643,52 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                 }
                 __syncwarp();
                 unsigned rest = __ballot_sync(kFull, has && !done);
+                if (rest && !have_tw) {
+                    tw = tie_words(gp, v, lane, g);
+                    have_tw = true;
+                }
+                if (deg <= kTileRows) {
+                    // Exact vote by the whole warp (lane = neighbour), two
+                    // unresolved pairs at a time as independent chains.
+                    const unsigned lt = (1u << lane) - 1u;
+                    const bool nb = lane < deg;
+                    const int pad = (int)(0x80000000u | (unsigned)lane);  // distinct, never a label
+                    while (rest) {
+                        const int la = __ffs(rest) - 1;
+                        rest &= rest - 1;
+                        const bool two = rest != 0u;
+                        const int lb = two ? __ffs(rest) - 1 : la;
+                        if (two) rest &= rest - 1;
+                        const int ia = __shfl_sync(kFull, i, la);
+                        const int ib = __shfl_sync(kFull, i, lb);
+                        const int xa = nb ? tile[lane * kTileStride + la] : pad;
+                        const int xb = (nb && two) ? tile[lane * kTileStride + lb] : pad;
+                        const unsigned pa = __match_any_sync(kFull, xa);
+                        const unsigned pb = __match_any_sync(kFull, xb);
+                        const unsigned ca = nb ? (unsigned)__popc(pa) : 0u;
+                        const unsigned cb = nb ? (unsigned)__popc(pb) : 0u;
+                        const unsigned ma = __reduce_max_sync(kFull, ca);
+                        const unsigned mb = __reduce_max_sync(kFull, cb);
+                        const unsigned da = __ballot_sync(kFull, ca == ma && (pa & lt) == 0u);
+                        const unsigned db = __ballot_sync(kFull, cb == mb && (pb & lt) == 0u);
+                        const uint32_t ua = __shfl_sync(kFull, word_of(tw, ia & 3), ia >> 2);
+                        const uint32_t ub = __shfl_sync(kFull, word_of(tw, ib & 3), ib >> 2);
+                        const int ta = __popc(da), tb = __popc(db);
+                        const int sa = ta == 1 ? __ffs(da) - 1 : select_kth_lane(da, xa, pick_index(ua, (uint32_t)ta));
+                        int sb = 0;
+                        if (two) sb = tb == 1 ? __ffs(db) - 1 : select_kth_lane(db, xb, pick_index(ub, (uint32_t)tb));
+                        const int ra = __shfl_sync(kFull, xa, sa);
+                        const int rb = __shfl_sync(kFull, xb, sb);
+                        if (lane == 0) {
+                            s_res[ia] = ra;
+                            if (two) s_res[ib] = rb;
+                        }
+                    }
+                }
                 while (rest) {
                     const int l = __ffs(rest) - 1;
                     rest &= rest - 1;
                     const int ic = __shfl_sync(kFull, i, l);
-                    if (!have_tw) {
-                        tw = tie_words(gp, v, lane, g);
-                        have_tw = true;
-                    }
                     const uint32_t u = __shfl_sync(kFull, word_of(tw, ic & 3), ic >> 2);
                     const int lab = warp_mode(gp, child, col_idx, beg, deg, tile + l, ic, hkey, hcnt, hbits, u);
                     if (lane == 0) s_res[ic] = lab;
