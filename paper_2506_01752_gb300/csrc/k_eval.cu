@@ -16,12 +16,18 @@
 // atomic returns the old total o, and (o + d)^2 - o^2 = 2 o d + d^2. Summed
 // over every addition these increments telescope to D_c^2 whatever the order
 // of the atomics, so S is exact and deterministic.
+//
+// Histogram layout: label-major, D of (individual i, label c) at c * W + i,
+// so that one atomic instruction of a warp (25 individuals of node v) lands
+// in few cache lines whenever individuals share v's label; or
+// individual-major, i * n + c (count * n cells, for fixed-size scratch).
 #include "mocd_internal.h"
 
 namespace mocd {
 
 namespace {
 
+template <bool LABEL_MAJOR>
 __global__ void __launch_bounds__(kBlock)
 evaluate_kernel(int n, int W, int count, const int32_t *__restrict__ row_ptr,
                 const int32_t *__restrict__ col_idx, const int32_t *__restrict__ labels,
@@ -47,6 +53,9 @@ evaluate_kernel(int n, int W, int count, const int32_t *__restrict__ row_ptr,
     int *nb = s_nb + (threadIdx.x & ~31);
     const unsigned lt = (1u << lane) - 1u;
 
+    auto cell = [&](int i, int c) -> size_t {
+        return LABEL_MAJOR ? (size_t)c * W + i : (size_t)i * n + c;
+    };
     uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
     unsigned long long q0 = 0, q1 = 0, q2 = 0, q3 = 0;
 
@@ -86,19 +95,19 @@ evaluate_kernel(int n, int W, int count, const int32_t *__restrict__ row_ptr,
         if (active && d > 0) {
             const unsigned dd = (unsigned)d;
             if (i0 + 0 < count) {
-                const unsigned long long o = atomicAdd(hist + (size_t)(i0 + 0) * n + own.x, dd);
+                const unsigned long long o = atomicAdd(hist + cell(i0 + 0, own.x), dd);
                 q0 += 2ull * o * d + d * d;
             }
             if (i0 + 1 < count) {
-                const unsigned long long o = atomicAdd(hist + (size_t)(i0 + 1) * n + own.y, dd);
+                const unsigned long long o = atomicAdd(hist + cell(i0 + 1, own.y), dd);
                 q1 += 2ull * o * d + d * d;
             }
             if (i0 + 2 < count) {
-                const unsigned long long o = atomicAdd(hist + (size_t)(i0 + 2) * n + own.z, dd);
+                const unsigned long long o = atomicAdd(hist + cell(i0 + 2, own.z), dd);
                 q2 += 2ull * o * d + d * d;
             }
             if (i0 + 3 < count) {
-                const unsigned long long o = atomicAdd(hist + (size_t)(i0 + 3) * n + own.w, dd);
+                const unsigned long long o = atomicAdd(hist + cell(i0 + 3, own.w), dd);
                 q3 += 2ull * o * d + d * d;
             }
         }
@@ -122,16 +131,19 @@ evaluate_kernel(int n, int W, int count, const int32_t *__restrict__ row_ptr,
 int grid_for_eval(int sms)
 {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, evaluate_kernel, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, evaluate_kernel<true>, kBlock, 0);
     if (per_sm < 1) per_sm = 1;
     return sms * per_sm;
 }
 
 cudaError_t launch_evaluate(int n, int W, int count, const int32_t *row_ptr, const int32_t *col_idx,
                             const int32_t *labels, uint32_t *hist, unsigned long long *acc,
-                            int grid, cudaStream_t s, const int32_t *order)
+                            int grid, cudaStream_t s, const int32_t *order, bool label_major)
 {
-    evaluate_kernel<<<grid, kBlock, 0, s>>>(n, W, count, row_ptr, col_idx, labels, hist, acc, order);
+    if (label_major)
+        evaluate_kernel<true><<<grid, kBlock, 0, s>>>(n, W, count, row_ptr, col_idx, labels, hist, acc, order);
+    else
+        evaluate_kernel<false><<<grid, kBlock, 0, s>>>(n, W, count, row_ptr, col_idx, labels, hist, acc, order);
     return cudaGetLastError();
 }
 

@@ -474,7 +474,7 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
     // The evaluation that follows accumulates into hist and acc: clear them
     // here, overlapped with this compute-bound kernel.
     {
-        const size_t words = (size_t)np * (size_t)gp.n;
+        const size_t words = (size_t)W * (size_t)gp.n;
         uint4 *h4 = reinterpret_cast<uint4 *>(hist);
         const size_t n4 = words >> 2;
         for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n4; t += (size_t)gridDim.x * blockDim.x)

@@ -39,7 +39,7 @@ struct PopState {
     int32_t *buf[2];          // P halves [n][W]: the P of R is buf[(g + 1) & 1]
     int32_t *q;               // Q [n][W]
     int32_t *c;               // post-crossover children [n][W]
-    uint32_t *hist;           // [Np][n]
+    uint32_t *hist;           // [n][W] label-major D of (individual, label)
     unsigned long long *acc;  // [2][kMaxPop]: intra (undirected edges), S
     int64_t *pk;              // [2][kMaxPop]: P keys k1 (m - intra), k2 (S), P order
     int64_t *rk;              // [2][2 kMaxPop]: R keys (P then Q) of the last selection
@@ -76,9 +76,12 @@ cudaError_t launch_crossover(const GenParams &gp, const PopState &ps, int grid, 
 // (degree descending), or NULL for 0..n-1 (evaluation only).
 cudaError_t launch_mutation(const GenParams &gp, const PopState &ps, const int32_t *row_ptr,
                             const int32_t *col_idx, const int32_t *order, int grid, cudaStream_t s);
+// hist: label-major [n][W] (label_major) or individual-major [count][n],
+// zeroed by the caller.
 cudaError_t launch_evaluate(int n, int W, int count, const int32_t *row_ptr, const int32_t *col_idx,
                             const int32_t *labels, uint32_t *hist, unsigned long long *acc,
-                            int grid, cudaStream_t s, const int32_t *order = nullptr);
+                            int grid, cudaStream_t s, const int32_t *order = nullptr,
+                            bool label_major = true);
 // mode 0: keys of a fresh P from acc, keep = identity; mode 1: R = P u Q,
 // environmental selection. Both then rank P and draw the next tournament.
 cudaError_t launch_select(const GenParams &gp, const PopState &ps, int mode, cudaStream_t s);

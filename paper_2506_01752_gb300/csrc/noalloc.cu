@@ -87,7 +87,8 @@ extern "C" int mocd_evaluate_noalloc(const int32_t *row_ptr, const int32_t *col_
         return MOCD_ERR_CUDA;
     int sms = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (launch_evaluate((int)n, W, count, row_ptr, col_idx, labels, hist, acc, grid_for_eval(sms), s) != cudaSuccess)
+    if (launch_evaluate((int)n, W, count, row_ptr, col_idx, labels, hist, acc, grid_for_eval(sms), s, nullptr,
+                        false) != cudaSuccess)
         return MOCD_ERR_CUDA;
     finish_keys_kernel<<<1, kMaxPop, 0, s>>>(count, acc, intra, sumsq);
     if (cudaGetLastError() != cudaSuccess) return MOCD_ERR_CUDA;

@@ -237,7 +237,7 @@ int prepare_population(mocd_ctx *c, const mocd_params *p)
         CK(cudaMemsetAsync(c->ps.q, 0, cells * sizeof(int32_t), c->stream));
         CK(cudaMemsetAsync(c->ps.buf[0], 0, cells * sizeof(int32_t), c->stream));
     }
-    const size_t hist_need = (size_t)p->pop_size * (size_t)c->n;
+    const size_t hist_need = (size_t)W * (size_t)c->n;
     {
         int rc = grow(c->stream, &c->ps.hist, &c->hist_cap, hist_need);
         if (rc) return rc;
@@ -329,7 +329,7 @@ int start_population(mocd_ctx *c, uint32_t base_gen)
     const GenParams &gp = c->gp;
     PopState &ps = c->ps;
     int32_t *phalf = ps.buf[(base_gen + 1u) & 1u];
-    int rc = clear_eval_state(c, ps.hist, (size_t)gp.np * (size_t)gp.n, ps.acc);
+    int rc = clear_eval_state(c, ps.hist, (size_t)gp.W * (size_t)gp.n, ps.acc);
     if (rc) return rc;
     CK(launch_evaluate(gp.n, gp.W, gp.np, c->d_row_ptr, c->d_col_idx, phalf, ps.hist, ps.acc,
                        c->grid_eval, c->stream));
@@ -880,7 +880,7 @@ int mocd_evaluate(mocd_ctx *c, int32_t count, const int32_t *labels, int64_t *in
     const size_t n = (size_t)c->n;
     if ((rc = grow(c->stream, &c->d_im, &c->im_cap, (size_t)batch * n))) return rc;
     if ((rc = grow(c->stream, &c->d_nm, &c->nm_cap, (size_t)kMaxPop * n))) return rc;
-    if ((rc = grow(c->stream, &c->d_eval_hist, &c->eval_hist_cap, (size_t)batch * n))) return rc;
+    if ((rc = grow(c->stream, &c->d_eval_hist, &c->eval_hist_cap, (size_t)((batch + 3) & ~3) * n))) return rc;
     if (!c->d_eval_acc) {
         void *q = nullptr;
         CK(cudaMallocAsync(&q, sizeof(unsigned long long) * 2 * kMaxPop, c->stream));
@@ -894,7 +894,7 @@ int mocd_evaluate(mocd_ctx *c, int32_t count, const int32_t *labels, int64_t *in
         CK(cudaMemcpyAsync(c->d_im, labels + (size_t)b0 * n, sizeof(int32_t) * (size_t)b * n,
                            cudaMemcpyHostToDevice, c->stream));
         CK(launch_to_node_major((int)n, W, b, c->d_im, c->d_nm, c->stream));
-        if ((rc = clear_eval_state(c, c->d_eval_hist, (size_t)b * n, c->d_eval_acc))) return rc;
+        if ((rc = clear_eval_state(c, c->d_eval_hist, (size_t)W * n, c->d_eval_acc))) return rc;
         CK(launch_evaluate((int)n, W, b, c->d_row_ptr, c->d_col_idx, c->d_nm, c->d_eval_hist, c->d_eval_acc,
                            grid, c->stream));
         CK(cudaMemcpyAsync(acc.data(), c->d_eval_acc, sizeof(unsigned long long) * 2 * kMaxPop,

@@ -56,7 +56,7 @@ struct Job {
 int64_t footprint(int64_t n, int64_t nnz, int32_t pop)
 {
     const int64_t W = (pop + 3) & ~3;
-    return 4 * n * W * 4 + (int64_t)pop * n * 4 + (n + 1) * 4 + nnz * 4 + n * 4 + (1 << 16);
+    return 4 * n * W * 4 + W * n * 4 + (n + 1) * 4 + nnz * 4 + n * 4 + (1 << 16);
 }
 
 }  // namespace
