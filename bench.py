@@ -378,7 +378,8 @@ def run_mine(args):
                                        device=dev if world > 1 else None)
         e2e = {"value": e2e_units / (e2e_t / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-               "job": f"graph upload + init + {args.steps} generations + front download, host buffers"}
+               "job": f"graph upload + init + {args.steps} generations + front download, host buffers",
+               "job_ms": round(e2e_t, 3)}
 
     mocd.destroy(ctx)
     cpu = None
