@@ -371,6 +371,68 @@ constexpr int kTileStride = 33;  // padded row of the per-warp label tile
 constexpr int kTileRows = 32;    // neighbours whose labels the tile keeps
 constexpr int kMutBlock = 128;   // mutation threads per block (shared memory bound)
 
+// Exact neighbour-majority of one pair whose node has 32 < deg <= 64: the
+// labels (two per lane: neighbour j = lane from the tile, 32 + lane from
+// global memory, INT_MAX beyond deg) are sorted across the warp with a
+// bitonic network; equal labels then form runs, whose lengths come from the
+// ballot of run starts. The tied runs of the largest length are already in
+// ascending label order, so the pick(u, t)-th of them is found by rank.
+__device__ __forceinline__ int warp_mode_sort64(const GenParams &gp, const int32_t *__restrict__ child,
+                                                const int32_t *__restrict__ col_idx, int beg, int deg,
+                                                const int *tile_col, int i, uint32_t tie_u)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    int a = tile_col[lane * kTileStride];
+    int b = 32 + lane < deg ? child[(size_t)__ldg(col_idx + beg + 32 + lane) * gp.W + i] : INT_MAX;
+    // Element e = lane holds a, e = 32 + lane holds b; ascending bitonic sort.
+#pragma unroll
+    for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j == 32) {
+                const int lo = min(a, b), hi = max(a, b);
+                a = lo;
+                b = hi;
+            } else {
+                const int pa = __shfl_xor_sync(kFull, a, j);
+                const int pb = __shfl_xor_sync(kFull, b, j);
+                const bool lower = (lane & j) == 0;
+                const bool asc_a = (lane & k) == 0;
+                const bool asc_b = ((lane + 32) & k) == 0;
+                a = (lower == asc_a) ? min(a, pa) : max(a, pa);
+                b = (lower == asc_b) ? min(b, pb) : max(b, pb);
+            }
+        }
+    }
+    // Run starts among the deg real elements (the padding sorts last).
+    const int prev_a = __shfl_up_sync(kFull, a, 1);
+    const int prev_b = __shfl_up_sync(kFull, b, 1);
+    const int last_a = __shfl_sync(kFull, a, 31);
+    const bool sa = lane < deg && (lane == 0 || a != prev_a);
+    const bool sb = 32 + lane < deg && (lane == 0 ? b != last_a : b != prev_b);
+    const unsigned long long starts =
+        ((unsigned long long)__ballot_sync(kFull, sb) << 32) | (unsigned long long)__ballot_sync(kFull, sa);
+    auto run_length = [&](int e) {
+        const unsigned long long after = e < 63 ? starts >> (e + 1) : 0ull;
+        return (after ? e + __ffsll((long long)after) : deg) - e;
+    };
+    const int ca = sa ? run_length(lane) : 0;
+    const int cb = sb ? run_length(32 + lane) : 0;
+    const int mx = (int)__reduce_max_sync(kFull, (unsigned)max(ca, cb));
+    const unsigned ta = __ballot_sync(kFull, ca == mx);
+    const unsigned tb = __ballot_sync(kFull, cb == mx);
+    const int na = __popc(ta);
+    const int t = na + __popc(tb);
+    const int kk = t > 1 ? (int)pick_index(tie_u, (uint32_t)t) : 0;
+    if (kk < na) {
+        const unsigned w = __ballot_sync(kFull, ((ta >> lane) & 1u) && __popc(ta & lt) == kk);
+        return __shfl_sync(kFull, a, __ffs(w) - 1);
+    }
+    const unsigned w = __ballot_sync(kFull, ((tb >> lane) & 1u) && __popc(tb & lt) == kk - na);
+    return __shfl_sync(kFull, b, __ffs(w) - 1);
+}
+
 // Exact neighbour-majority of one (node, child) pair by the whole warp
 // (lane = neighbour); used for the pairs without a strict majority.
 __device__ __forceinline__ int warp_mode(const GenParams &gp, const int32_t *__restrict__ child,
@@ -393,6 +455,7 @@ __device__ __forceinline__ int warp_mode(const GenParams &gp, const int32_t *__r
         const int src = t == 1 ? __ffs(cand) - 1 : select_kth_lane(cand, x, pick_index(tie_u, (uint32_t)t));
         return __shfl_sync(kFull, x, src);
     }
+    if (deg <= 64) return warp_mode_sort64(gp, child, col_idx, beg, deg, tile_col, i, tie_u);
     const int HS = 1 << hbits;
     const int per_lane = HS >> 5;
     for (int e = lane; e < HS; e += 32) {

@@ -53,6 +53,8 @@ GRAPHS = {
     "lfr-3k": lambda: synth.lfr_style(3000, 20, 50, 0.3, seed=2)[:2],
     "star": lambda: star_plus(),
     "pair": lambda: synth.csr_from_edges(2, [0], [1]),
+    # every degree in 33..64: the sorting-network vote of the mutation fallback
+    "dense": lambda: synth.planted_partition(2, 80, 0.5, 0.1, seed=5)[:2],
 }
 
 
@@ -145,6 +147,8 @@ def test_init_matches_oracle(gname, init_mode):
     ("pair", 3, dict(pop_size=100)),
     ("fig2", 5, dict(pop_size=127, n_parents=2)),
     ("fig2", 4, dict(pop_size=64, n_parents=7, p_mutation=0.5)),
+    ("dense", 5, dict(pop_size=100)),
+    ("dense", 3, dict(pop_size=64, p_mutation=1.0, seed=3)),
     # hybrid initialisation (singletons + one neighbour-majority step)
     ("star", 3, dict(pop_size=24, init_mode=1)),
     ("planted-1k", 4, dict(pop_size=100, init_mode=1)),
