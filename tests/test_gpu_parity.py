@@ -53,8 +53,11 @@ GRAPHS = {
     "lfr-3k": lambda: synth.lfr_style(3000, 20, 50, 0.3, seed=2)[:2],
     "star": lambda: star_plus(),
     "pair": lambda: synth.csr_from_edges(2, [0], [1]),
-    # every degree in 33..64: the sorting-network vote of the mutation fallback
+    # every degree in 33..64 (the sorting-network vote of the mutation
+    # fallback), 65..128 and 129..256 (its shared count table)
     "dense": lambda: synth.planted_partition(2, 80, 0.5, 0.1, seed=5)[:2],
+    "dense128": lambda: synth.planted_partition(2, 150, 0.6, 0.1, seed=7)[:2],
+    "dense256": lambda: synth.planted_partition(2, 260, 0.65, 0.12, seed=8)[:2],
 }
 
 
@@ -149,6 +152,10 @@ def test_init_matches_oracle(gname, init_mode):
     ("fig2", 4, dict(pop_size=64, n_parents=7, p_mutation=0.5)),
     ("dense", 5, dict(pop_size=100)),
     ("dense", 3, dict(pop_size=64, p_mutation=1.0, seed=3)),
+    ("dense128", 4, dict(pop_size=100)),
+    ("dense128", 2, dict(pop_size=48, p_mutation=1.0, seed=4)),
+    ("dense256", 3, dict(pop_size=64)),
+    ("dense256", 2, dict(pop_size=32, p_mutation=1.0, seed=5)),
     # hybrid initialisation (singletons + one neighbour-majority step)
     ("star", 3, dict(pop_size=24, init_mode=1)),
     ("planted-1k", 4, dict(pop_size=100, init_mode=1)),
