@@ -46,6 +46,21 @@ def star_plus(n_leaves=300, extra=40, seed=0):
     return rp, ci
 
 
+def hub_of_degree(d, extra=300, seed=0):
+    """Node 0 adjacent to nodes 1..d, plus a sparse random part among them."""
+    rng = np.random.default_rng(seed)
+    n = d + 1
+    a = rng.integers(1, n, extra)
+    b = rng.integers(1, n, extra)
+    return synth.csr_from_edges(n, np.concatenate([np.zeros(d, np.int64), a]),
+                                np.concatenate([np.arange(1, n), b]))
+
+
+def complete_graph(k):
+    u, v = np.triu_indices(k, 1)
+    return synth.csr_from_edges(k, u, v)
+
+
 GRAPHS = {
     "fig2": lambda: graph(load("fig2_toy_graph.txt")),
     "appE": lambda: graph(load("appE_operator_example.txt")),
@@ -172,6 +187,47 @@ def test_generations_match_oracle(gname, G, kw):
             mocd.generation(h, 1)
             ref = oracle.run(rp, ci, op, ref, 1)
             _compare_state(h, ref, m)
+
+
+@pytest.mark.parametrize("gname,G,kw", [
+    ("hub512", 3, dict(pop_size=24, p_mutation=1.0)),       # the largest degree the build takes
+    ("hub512", 2, dict(pop_size=40, seed=(1 << 40) + 7)),
+    ("one-edge", 3, dict(pop_size=20, p_mutation=1.0)),     # thousands of isolated nodes
+    ("k40", 4, dict(pop_size=30, p_mutation=0.5)),          # one dense community, degree 39
+    ("k33", 3, dict(pop_size=16, p_mutation=1.0)),          # degree exactly 32
+    ("lfr-3k", 2, dict(pop_size=50, seed=0xDEADBEEF12345678)),  # both key words non-zero
+])
+def test_extreme_graphs_match_oracle(gname, G, kw):
+    rp, ci = {
+        "hub512": lambda: hub_of_degree(512),
+        "one-edge": lambda: synth.csr_from_edges(3000, [17], [2950]),
+        "k40": lambda: complete_graph(40),
+        "k33": lambda: complete_graph(33),
+        "lfr-3k": GRAPHS["lfr-3k"],
+    }[gname]()
+    gp, op = _params(**kw)
+    m = int(rp[-1] // 2)
+    ref = oracle.population_init(rp, ci, op)
+    with Ctx(rp, ci) as h:
+        mocd.population_init(h, gp)
+        _compare_state(h, ref, m)
+        for step in range(G):
+            mocd.generation(h, 1)
+            ref = oracle.run(rp, ci, op, ref, 1)
+            _compare_state(h, ref, m)
+
+
+def test_degree_above_the_limit_rejected():
+    """Degree 513 exceeds the mutation count table: the graph uploads (it is
+    valid) but a population on it is refused with INVALID_ARG."""
+    rp, ci = hub_of_degree(513)
+    with Ctx(rp, ci) as h:
+        with pytest.raises(mocd.MocdError) as e:
+            mocd.population_init(h, mocd.Params(pop_size=8))
+        assert e.value.status == -1
+        gi, gs = mocd.evaluate(h, synth.random_labels(rp.size - 1, 3, seed=1))
+        oi, os_ = oracle.objectives(rp, ci, synth.random_labels(rp.size - 1, 3, seed=1))
+        assert np.array_equal(gi, oi) and np.array_equal(gs, os_)
 
 
 def test_planted_full_run_front_bit_exact():
