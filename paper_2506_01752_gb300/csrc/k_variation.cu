@@ -323,9 +323,13 @@ crossover_kernel(GenParams gp, const int32_t *buf0, const int32_t *buf1, int32_t
 // deg(v) > 0; it then takes the most frequent label among its neighbours in
 // the post-crossover child (synchronous: all reads come from `child`), the
 // tie among the t most frequent labels broken by the MTIE word (the
-// pick(u, t)-th smallest). Degree <= 32: one neighbour per lane and
-// __match_any_sync groups equal labels. Degree > 32: a per-warp open-addressing
-// count table in shared memory.
+// pick(u, t)-th smallest). A warp takes a node; its lanes take the node's
+// selected children. Each lane summarises its pair's neighbour labels with a
+// three-counter Misra-Gries pass and recounts the survivors exactly, which
+// settles the pair whenever the best count c has 4 c > deg. The other pairs
+// get an exact vote by the whole warp: degree <= 32, one neighbour per lane
+// grouped by __match_any_sync; 33..64, a sorting network over two labels per
+// lane; beyond, a count table in shared memory.
 // ---------------------------------------------------------------------------
 
 // The k-th smallest of the distinct labels held by the lanes of `cand`: the
@@ -433,8 +437,11 @@ __device__ __forceinline__ int warp_mode_sort64(const GenParams &gp, const int32
     return __shfl_sync(kFull, b, __ffs(w) - 1);
 }
 
-// Exact neighbour-majority of one (node, child) pair by the whole warp
-// (lane = neighbour); used for the pairs without a strict majority.
+// Exact neighbour-majority of one pair of a node with degree > 32 by the
+// whole warp: 33..64 by the sorting network above; beyond that a per-warp
+// open-addressing count table in shared memory (inserts aggregated per
+// distinct label of a 32-neighbour chunk with __match_any_sync), then the
+// largest count, the tied labels and the pick(u, t)-th smallest of them.
 __device__ __forceinline__ int warp_mode(const GenParams &gp, const int32_t *__restrict__ child,
                                          const int32_t *__restrict__ col_idx, int beg, int deg,
                                          const int *tile_col, int i, int *hkey, int *hcnt, int hbits,
@@ -442,19 +449,6 @@ __device__ __forceinline__ int warp_mode(const GenParams &gp, const int32_t *__r
 {
     const int lane = threadIdx.x & 31;
     const int W = gp.W;
-    if (deg <= 32) {
-        // tile_col[j * kTileStride] holds this pair's label of neighbour j
-        // (for the first kTileRows neighbours).
-        const unsigned lt = (1u << lane) - 1u;
-        const int x = lane < deg ? tile_col[lane * kTileStride] : (int)(0x80000000u | lane);
-        const unsigned peers = __match_any_sync(kFull, x);
-        const unsigned cnt = lane < deg ? __popc(peers) : 0u;
-        const unsigned mx = __reduce_max_sync(kFull, cnt);
-        const unsigned cand = __ballot_sync(kFull, lane < deg && cnt == mx && (peers & lt) == 0);
-        const int t = __popc(cand);
-        const int src = t == 1 ? __ffs(cand) - 1 : select_kth_lane(cand, x, pick_index(tie_u, (uint32_t)t));
-        return __shfl_sync(kFull, x, src);
-    }
     if (deg <= 64) return warp_mode_sort64(gp, child, col_idx, beg, deg, tile_col, i, tie_u);
     const int HS = 1 << hbits;
     const int per_lane = HS >> 5;
