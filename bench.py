@@ -51,6 +51,8 @@ def parse_args(argv=None):
     ap.add_argument("--mu", type=float, default=0.3)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--timing-every", type=int, default=5,
+                    help="every k-th timed step runs the generation graph with per-stage events")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=80, help="serving trace length (--workload serve)")
     ap.add_argument("--hbm-budget-gb", type=int, default=64, help="server device-memory budget")
@@ -308,9 +310,12 @@ def run_mine(args):
     index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) if world == 1 else local
     sampler = ClockSampler(index)
     sampler.start()
-    # Warm-up: W generations, then a short pre-roll so that clocks settle.
-    for _ in range(args.warmup):
+    # Warm-up: W generations (both generation graphs, with and without stage
+    # events, get captured here), then a short pre-roll so that clocks settle.
+    for w in range(args.warmup):
+        mocd.set_timing(ctx, w % 2 == 0)
         mocd.generation(ctx, 1)
+    mocd.set_timing(ctx, False)
     t_end = time.perf_counter() + args.preroll_s
     pre = 0
     while time.perf_counter() < t_end:
@@ -321,9 +326,15 @@ def run_mine(args):
     barrier(world)
     torch.cuda.synchronize()
 
+    # Per-stage durations come from the steps that run the graph with stage
+    # events (every --timing-every-th step): those events cost the step about
+    # 20 us, so the other steps run the plain graph. Both are the same kernels.
     step_ms = []
     stages = {s: [] for s in mocd.STAGES}
-    for _ in range(args.steps):
+    every = max(1, args.timing_every)
+    for k in range(args.steps):
+        timed = k % every == 0
+        mocd.set_timing(ctx, timed)
         with torch.cuda.stream(stream):
             flush.zero_()  # L2 flush between timed steps, outside the events
         ev0.record(stream)
@@ -331,8 +342,9 @@ def run_mine(args):
         ev1.record(stream)
         ev1.synchronize()
         step_ms.append(ev0.elapsed_time(ev1))
-        for s, v in mocd.kernel_times(ctx).items():
-            stages[s].append(v)
+        if timed:
+            for s, v in mocd.kernel_times(ctx).items():
+                stages[s].append(v)
     torch.cuda.synchronize()
     barrier(world)
     clocks = sampler.stop()
@@ -352,7 +364,8 @@ def run_mine(args):
                 "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": recorded_traffic(dominant, args.workload),
                 "algorithmic_bytes_per_launch": alg[dominant],
-                "stage_ms": {k: round(v, 5) for k, v in mean_stage.items()}}
+                "stage_ms": {k: round(v, 5) for k, v in mean_stage.items()},
+                "stage_events_every": every}
     # The objective (evaluation) kernel, against the same HBM roofline.
     ev_achieved = alg["evaluate"] / (kernels["evaluate"] / 1e3) / 1e9
     roofline_objective = {"bound": "hbm", "kernel": "evaluate", "achieved": ev_achieved, "peak": peak,

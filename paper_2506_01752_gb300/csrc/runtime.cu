@@ -56,8 +56,11 @@ struct mocd_ctx {
     int32_t version = 0;    // bumped whenever the population is (re)built
     uint32_t gen_host_value = 0;
 
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t graph_exec = nullptr;
+    // Generation graphs: [0] plain, [1] with stage events (timing); each is
+    // captured on first use and both stay valid until the population or the
+    // launch shape changes.
+    cudaGraph_t graph[2] = {};
+    cudaGraphExec_t graph_exec[2] = {};
     bool timing = false;
     bool timing_valid = false;
     cudaEvent_t ev[kStages + 1] = {};
@@ -121,12 +124,19 @@ int grow(cudaStream_t st, T **p, size_t *cap, size_t need)
     return MOCD_OK;
 }
 
+void drop_graphs(mocd_ctx *c)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (c->graph_exec[k]) cudaGraphExecDestroy(c->graph_exec[k]);
+        if (c->graph[k]) cudaGraphDestroy(c->graph[k]);
+        c->graph_exec[k] = nullptr;
+        c->graph[k] = nullptr;
+    }
+}
+
 void free_population(mocd_ctx *c)
 {
-    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
-    if (c->graph) cudaGraphDestroy(c->graph);
-    c->graph_exec = nullptr;
-    c->graph = nullptr;
+    drop_graphs(c);
     dev_free(c->ps.buf[0], c->stream);
     dev_free(c->ps.buf[1], c->stream);
     dev_free(c->ps.q, c->stream);
@@ -181,12 +191,7 @@ int prepare_population(mocd_ctx *c, const mocd_params *p)
 {
     const int W = (p->pop_size + 3) & ~3;
     const size_t cells = (size_t)c->n * (size_t)W;
-    if (c->ready || c->graph_exec) {
-        if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
-        if (c->graph) cudaGraphDestroy(c->graph);
-        c->graph_exec = nullptr;
-        c->graph = nullptr;
-    }
+    drop_graphs(c);
     if (c->pop_cells != cells) {
         free_population(c);
         int32_t *b[4] = {};
@@ -302,12 +307,11 @@ int issue_generation(mocd_ctx *c, cudaStream_t st, bool events)
     return MOCD_OK;
 }
 
+// Capture the generation graph of the current timing mode (if missing).
 int build_graph(mocd_ctx *c)
 {
-    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
-    if (c->graph) cudaGraphDestroy(c->graph);
-    c->graph_exec = nullptr;
-    c->graph = nullptr;
+    const int k = c->timing ? 1 : 0;
+    if (c->graph_exec[k]) return MOCD_OK;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     int rc = issue_generation(c, c->stream, c->timing);
     cudaGraph_t g = nullptr;
@@ -317,8 +321,8 @@ int build_graph(mocd_ctx *c)
         return rc;
     }
     CK(e);
-    c->graph = g;
-    CK(cudaGraphInstantiate(&c->graph_exec, g, 0));
+    c->graph[k] = g;
+    CK(cudaGraphInstantiate(&c->graph_exec[k], g, 0));
     return MOCD_OK;
 }
 
@@ -338,6 +342,7 @@ int start_population(mocd_ctx *c, uint32_t base_gen)
     CK(launch_select(gp, ps, 0, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->host_gen = (int32_t)base_gen;
+    drop_graphs(c);
     rc = build_graph(c);
     if (rc) return rc;
     c->ready = true;
@@ -743,7 +748,12 @@ int mocd_generation(mocd_ctx *c, int32_t n_generations)
 {
     if (!c || n_generations < 0) return MOCD_ERR_INVALID_ARG;
     if (!c->ready) return MOCD_ERR_NOT_READY;
-    for (int32_t k = 0; k < n_generations; ++k) CK(cudaGraphLaunch(c->graph_exec, c->stream));
+    const int g = c->timing ? 1 : 0;
+    if (!c->graph_exec[g]) {
+        const int rc = build_graph(c);
+        if (rc) return rc;
+    }
+    for (int32_t k = 0; k < n_generations; ++k) CK(cudaGraphLaunch(c->graph_exec[g], c->stream));
     c->host_gen += n_generations;
     if (n_generations > 0 && c->timing) c->timing_valid = true;
     return MOCD_OK;
@@ -922,10 +932,8 @@ int mocd_set_timing(mocd_ctx *c, int32_t enable)
     if (want == c->timing) return MOCD_OK;
     c->timing = want;
     c->timing_valid = false;
-    if (c->ready) {
-        CK(cudaStreamSynchronize(c->stream));
-        return build_graph(c);
-    }
+    // Switching between the two graphs costs nothing once both exist.
+    if (c->ready && !c->graph_exec[want ? 1 : 0]) return build_graph(c);
     return MOCD_OK;
 }
 
@@ -1090,6 +1098,7 @@ int mocd_batch_autotune(mocd_batch *b, int32_t generations_per_trial, int32_t *n
         c->nodes_per_warp = best;
         size_grids(c);
         // Keep each member's own generation graph in the same launch shape.
+        drop_graphs(c);
         if ((rc = build_graph(c))) return rc;
     }
     if ((rc = batch_build(b))) return rc;
