@@ -164,32 +164,42 @@ __device__ void rank_crowd_order(SelShared &S, int N, bool known_rank)
         const int gstart = block_max_scan(S, head ? t : 0);
 
         // (2) Fronts. A remaining point is dominated iff some remaining point
-        // sorted before its group has k2 <= its k2.
+        // sorted before its group has k2 <= its k2. (3) Each front, once
+        // found, is laid out contiguously after the earlier ones, its members
+        // in sorted (k1, k2, index) order: position = points placed so far +
+        // members of the front at earlier sorted positions.
+        const int lane = t & 31, w = t >> 5;
+        const unsigned lt = (1u << lane) - 1u;
         bool rem = real;
         int myrank = 0;
+        int placed = 0;  // points of the fronts found so far (block-uniform)
         for (int r = 1;; ++r) {
             const unsigned long long pm = block_min_scan(S, rem ? my2 : kInf64);
             S.sa[t] = pm;
             __syncthreads();
             const unsigned long long before = gstart > 0 ? S.sa[gstart - 1] : kInf64;
             const bool inf = rem && before > my2;
+            const unsigned bal = __ballot_sync(kFull, inf);
+            if (lane == 0) S.wscan[w] = (unsigned long long)__popc(bal);
+            __syncthreads();
+            int off = placed, tot = 0;
+#pragma unroll
+            for (int q = 0; q < kSelWarps; ++q) {
+                const int c = (int)S.wscan[q];
+                off += q < w ? c : 0;
+                tot += c;
+            }
             if (inf) {
+                S.ib[off + __popc(bal & lt)] = id;
                 myrank = r;
                 rem = false;
             }
-            __syncthreads();
+            placed += tot;
             if (!__syncthreads_or(rem)) break;
         }
         if (real) S.rank[id] = myrank;
-        S.ia[t] = id;  // point at sorted position t
         __syncthreads();
-
-        // (3) Fronts contiguous, each in (k1, index) order: sort by (rank, position).
-        Key f;
-        f.a = ((real ? (unsigned long long)myrank : 0xffffffffull) << 32) | (unsigned long long)t;
-        f.b = 0;
-        f = block_sort(S, f, size);
-        e = S.ia[(int)(f.a & 0xffffffffull)];
+        e = t < N ? S.ib[t] : N;
     } else {
         // Ranks known: one sort by (rank, k1, k2, index), packed as
         // rank:9 | k1:31 | hi24(k2) and lo40(k2) | index:24.
