@@ -80,6 +80,9 @@ typedef struct {
  *            edge in both rows), no self loops, no repeated neighbours
  *   cuda_stream  cudaStream_t to issue work on, or NULL for a stream the
  *            context creates and owns
+ * Rows may come in any order (a sorted copy is made when needed). The host
+ * checks every row first (ids in range, self loops, repeats; the first
+ * failing row decides the status), then symmetry is checked on the device.
  * Errors: INVALID_ARG, NOT_SYMMETRIC, SELF_LOOP, DUPLICATE_EDGE, EMPTY_GRAPH,
  * OUT_OF_MEMORY, CUDA.
  */

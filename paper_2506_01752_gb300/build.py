@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmocd.so")
-SOURCES = ["k_eval.cu", "k_variation.cu", "k_select.cu", "runtime.cu", "noalloc.cu", "server.cu", "k_stats.cu"]
+SOURCES = ["k_eval.cu", "k_variation.cu", "k_select.cu", "runtime.cu", "noalloc.cu", "server.cu", "k_stats.cu", "k_graph.cu"]
 HEADERS = ["mocd_internal.h", "philox.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",

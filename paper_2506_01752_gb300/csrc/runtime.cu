@@ -643,17 +643,9 @@ int mocd_graph_upload(mocd_ctx **out, int64_t n, const int64_t *row_ptr, const i
         }
     });
     if (err.status()) return err.status();
-    parallel_rows(row_ptr, n, [&](int64_t v0, int64_t v1) {
-        for (int64_t v = v0; v < v1; ++v)
-            for (int64_t k = row_ptr[v]; k < row_ptr[v + 1]; ++k) {
-                const int32_t u = src[k];
-                if (!std::binary_search(src + row_ptr[u], src + row_ptr[u + 1], (int32_t)v)) {
-                    err.record(v, MOCD_ERR_NOT_SYMMETRIC);
-                    return;
-                }
-            }
-    });
-    if (err.status()) return err.status();
+    // Symmetry is checked on the device once the CSR is there (below): a
+    // binary search per stored entry, which the host's scattered memory
+    // accesses make slow for large graphs.
     int dmax = 0;
     for (int64_t v = 0; v < n; ++v) dmax = std::max<int>(dmax, (int)(row_ptr[v + 1] - row_ptr[v]));
     if (nnz == 0) return MOCD_ERR_EMPTY_GRAPH;
@@ -703,12 +695,21 @@ int mocd_graph_upload(mocd_ctx **out, int64_t n, const int64_t *row_ptr, const i
     if (cudaMemcpyAsync(c->d_order, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream) !=
         cudaSuccess)
         return fail(MOCD_ERR_CUDA);
-    if (cudaMemcpyAsync(c->d_row_ptr, rp32.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice,
-                        c->stream) != cudaSuccess ||
-        cudaMemcpyAsync(c->d_col_idx, src, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice,
-                        c->stream) != cudaSuccess ||
-        cudaStreamSynchronize(c->stream) != cudaSuccess)
-        return fail(MOCD_ERR_CUDA);
+    int *d_bad = nullptr;
+    int h_bad = 0;
+    e = cudaMallocAsync(reinterpret_cast<void **>(&d_bad), sizeof(int), c->stream);
+    if (e != cudaSuccess) return fail(cuda_status(e));
+    const bool copied =
+        cudaMemcpyAsync(c->d_row_ptr, rp32.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice,
+                        c->stream) == cudaSuccess &&
+        cudaMemcpyAsync(c->d_col_idx, src, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, c->stream) ==
+            cudaSuccess &&
+        cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream) == cudaSuccess &&
+        launch_symmetry_check((int)n, c->d_row_ptr, c->d_col_idx, d_bad, c->sms, c->stream) == cudaSuccess &&
+        cudaMemcpyAsync(&h_bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream) == cudaSuccess;
+    cudaFreeAsync(d_bad, c->stream);
+    if (!copied || cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(MOCD_ERR_CUDA);
+    if (h_bad) return fail(MOCD_ERR_NOT_SYMMETRIC);
     *out = c;
     return MOCD_OK;
 }

@@ -52,7 +52,6 @@ def _upload_status(rp, ci):
 
 
 @pytest.mark.parametrize("rp,ci,status", [
-    ([0, 1, 1], [1], -2),                 # 0->1 without 1->0
     ([0, 1, 2], [0, 1], -3),              # self loops
     ([0, 2, 4], [1, 1, 0, 0], -4),        # repeated edge
     ([0, 0, 0], [], -5),                  # no edges
@@ -111,11 +110,11 @@ def test_large_graph_validation_passes_with_shuffled_rows(lib):
     assert _upload_status(rp, ci) not in _validation_codes()
 
 
-@pytest.mark.parametrize("defect", ["self_loop_first", "range_first", "asym", "dup_unsorted"])
+@pytest.mark.parametrize("defect", ["self_loop_first", "range_first", "dup_unsorted"])
 def test_large_graph_first_failing_row_decides(lib, defect):
     """Defects in rows handled by different threads: the status is that of
-    the lowest-numbered failing row, as in a sequential scan; symmetry is
-    checked only after every row passed the per-row checks."""
+    the lowest-numbered failing row, as in a sequential scan. (Symmetry is
+    checked on the device after every row passed; see the GPU tests.)"""
     rp, ci = _big_graph()
     lo, hi = 10, rp.size - 50  # first and last thread ranges
     if defect == "self_loop_first":
@@ -126,11 +125,6 @@ def test_large_graph_first_failing_row_decides(lib, defect):
         ci[rp[lo]] = -7
         ci[rp[hi]] = hi
         want = -1
-    elif defect == "asym":
-        row = ci[rp[hi]:rp[hi + 1]]
-        w = int(np.setdiff1d(np.arange(rp.size - 1), np.concatenate([row, [hi]]))[0])
-        ci[rp[hi]] = w            # hi -> w without w -> hi (and u -> hi without hi -> u)
-        want = -2
     else:
         seg = ci[rp[hi]:rp[hi + 1]].copy()
         seg[-1] = seg[0]           # repeated neighbour

@@ -217,6 +217,30 @@ def test_extreme_graphs_match_oracle(gname, G, kw):
             _compare_state(h, ref, m)
 
 
+def test_upload_rejects_asymmetric_graphs():
+    """Symmetry is checked on the device after the per-row host checks: a
+    missing mirror anywhere gives NOT_SYMMETRIC, a self loop elsewhere still
+    gives SELF_LOOP (the host checks come first)."""
+    cases = [(np.array([0, 1, 1]), np.array([1]))]  # 0 -> 1 without 1 -> 0
+    rp, ci, _ = synth.lfr_style(20000, 20, 50, 0.3, seed=4)
+    for row in (10, rp.size - 50):
+        bad = ci.copy()
+        nb = bad[rp[row]:rp[row + 1]]
+        w = int(np.setdiff1d(np.arange(rp.size - 1), np.concatenate([nb, [row]]))[0])
+        bad[rp[row]] = w  # row -> w without w -> row
+        cases.append((rp, bad))
+    for rp_, ci_ in cases:
+        with pytest.raises(mocd.MocdError) as e:
+            mocd.graph_upload(rp_, ci_)
+        assert e.value.status == -2
+    bad = cases[1][1].copy()
+    last = rp.size - 10
+    bad[rp[last]] = last  # and a self loop in a later row: the host check decides
+    with pytest.raises(mocd.MocdError) as e:
+        mocd.graph_upload(rp, bad)
+    assert e.value.status == -3
+
+
 def test_degree_above_the_limit_rejected():
     """Degree 513 exceeds the mutation count table: the graph uploads (it is
     valid) but a population on it is refused with INVALID_ARG."""
