@@ -335,6 +335,30 @@ def test_kernel_timing_reports_every_stage():
     assert np.array_equal(a[0], b[0])
 
 
+def test_timing_toggled_every_generation_matches_oracle():
+    """The plain and the stage-timed generation graphs coexist; switching
+    between them every generation (as the benchmark does) changes nothing in
+    the results, and stage times exist only after a timed launch."""
+    rp, ci = GRAPHS["lfr-3k"]()
+    gp, op = _params(pop_size=40, seed=17)
+    m = int(rp[-1] // 2)
+    ref = oracle.population_init(rp, ci, op)
+    with Ctx(rp, ci) as h:
+        mocd.population_init(h, gp)
+        for step in range(6):
+            timed = step % 2 == 1
+            mocd.set_timing(h, timed)
+            mocd.generation(h, 1)
+            if timed:
+                assert set(mocd.kernel_times(h)) == set(mocd.STAGES)
+            else:
+                with pytest.raises(mocd.MocdError) as e:
+                    mocd.kernel_times(h)
+                assert e.value.status == -9
+            ref = oracle.run(rp, ci, op, ref, 1)
+            _compare_state(h, ref, m)
+
+
 def test_invalid_params_rejected():
     rp, ci = GRAPHS["planted-1k"]()
     with Ctx(rp, ci) as h:
