@@ -83,7 +83,8 @@ struct mocd_server {
 
 namespace {
 
-void release(mocd_server *s, Job *j)
+// Frees a job's device state (its context and completion event).
+void release(Job *j)
 {
     if (j->done) cudaEventDestroy(j->done);
     j->done = nullptr;
@@ -93,7 +94,7 @@ void release(mocd_server *s, Job *j)
 
 void finish(mocd_server *s, Job *j, int state, int status)
 {
-    release(s, j);
+    release(j);
     s->used -= j->footprint;
     j->state = state;
     j->status = status;
@@ -351,7 +352,7 @@ void mocd_server_destroy(mocd_server *s)
     s->cv_admit.notify_all();
     for (std::thread &t : s->threads) t.join();
     for (auto &kv : s->jobs) {
-        release(s, kv.second);
+        release(kv.second);
         delete kv.second;
     }
     delete s;
