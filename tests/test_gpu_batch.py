@@ -85,3 +85,41 @@ def test_batch_rejects_bad_members():
         assert e.value.status == -1
     finally:
         mocd.destroy(c)
+
+
+def test_full_batch_of_64_sampled_against_oracle():
+    """The batched-jobs workload at full size (64 uneven jobs, n from 1e3 to
+    5e4, N_p = 100 each, seeds as the benchmark uses them), in the launch shape
+    the autotuner picks: two batched generations, then six jobs (the
+    smallest, the largest and four in between) compared bit for bit with the
+    oracle run of the same job."""
+    insts = synth.batch_instances(64, seed=0)
+    ctxs = [mocd.graph_upload(rp, ci) for rp, ci, _, _ in insts]
+    try:
+        for k, c in enumerate(ctxs):
+            mocd.population_init(c, mocd.Params(seed=k))
+        b = mocd.batch_create(ctxs)
+        mocd.batch_autotune(b, 1)
+        mocd.batch_destroy(b)
+        for k, c in enumerate(ctxs):
+            mocd.population_init(c, mocd.Params(seed=k))
+        b = mocd.batch_create(ctxs)
+        try:
+            mocd.batch_generation(b, 2)
+            mocd.batch_synchronize(b)
+        finally:
+            mocd.batch_destroy(b)
+        sizes = np.array([rp.size - 1 for rp, _, _, _ in insts])
+        order = np.argsort(sizes)
+        sample = sorted({int(order[0]), int(order[-1]), *[int(order[q]) for q in (13, 29, 41, 55)]})
+        for k in sample:
+            rp, ci, _, _ = insts[k]
+            op = oracle.Params(seed=k)
+            ref = oracle.run(rp, ci, op, oracle.population_init(rp, ci, op), 2)
+            labels, k1, k2, gen = mocd.get_population(ctxs[k])
+            assert gen == 2
+            assert np.array_equal(k1, ref.k1) and np.array_equal(k2, ref.k2), k
+            assert np.array_equal(labels, ref.labels), k
+    finally:
+        for c in ctxs:
+            mocd.destroy(c)

@@ -68,13 +68,13 @@ def test_server_results_equal_alone(budget, max_running, background):
             assert np.array_equal(got.f1, ref.f1) and np.array_equal(got.f2, ref.f2)
         if background is None:
             assert srv.state(ids[0])[0] == mocd.Server.DONE
-        # and the oracle agrees with one of them
-        (rp, ci), kw, G = jobs[1]
-        op = oracle.Params(**kw)
-        st = oracle.run(rp, ci, op, oracle.population_init(rp, ci, op), G)
-        members, best = oracle.pareto_front(st, int(rp[-1] // 2))
-        got = srv.result(ids[1])
-        assert got.best == best and np.array_equal(got.labels, st.labels[members])
+        # and the oracle agrees with every one of them
+        for jid, ((rp, ci), kw, G) in zip(ids, jobs):
+            op = oracle.Params(**kw)
+            st = oracle.run(rp, ci, op, oracle.population_init(rp, ci, op), G)
+            members, best = oracle.pareto_front(st, int(rp[-1] // 2))
+            got = srv.result(jid)
+            assert got.best == best and np.array_equal(got.labels, st.labels[members])
     finally:
         srv.close()
 
@@ -85,11 +85,13 @@ def test_server_failures():
         big_rp, big_ci, _ = synth.workload("planted-1k", seed=0)
         j_big = srv.submit(big_rp, big_ci, mocd.Params(), 5)          # footprint > budget
         j_bad = srv.submit([0, 1, 2], [0, 1], mocd.Params(pop_size=4), 5)  # self loops
+        j_asym = srv.submit([0, 1, 1], [1], mocd.Params(pop_size=4), 5)  # 0 -> 1 only
         rp, ci = graph(load("appE_operator_example.txt"))
         j_ok = srv.submit(rp, ci, mocd.Params(pop_size=8), 5)
-        _drain(srv, [j_big, j_bad, j_ok], 4)
+        _drain(srv, [j_big, j_bad, j_asym, j_ok], 4)
         assert srv.state(j_big) == (mocd.Server.FAILED, -6)
         assert srv.state(j_bad) == (mocd.Server.FAILED, -3)
+        assert srv.state(j_asym) == (mocd.Server.FAILED, -2)
         assert srv.state(j_ok)[0] == mocd.Server.DONE
         with pytest.raises(mocd.MocdError) as e:
             srv.result(j_big)
