@@ -23,8 +23,9 @@ __all__ = [
     "get_population", "get_offspring", "set_population", "evaluate", "synchronize",
     "set_timing", "kernel_times", "info", "destroy", "status_string", "evaluate_noalloc",
     "batch_create", "batch_generation", "batch_autotune", "batch_synchronize", "batch_destroy",
-    "Server",
-    "STAGES",
+    "Server", "FrontStats", "front_stats", "select_solution",
+    "SELECT_MODULARITY", "SELECT_COMMUNITIES", "SELECT_SIZE_VARIANCE", "SELECT_MEAN_CONDUCTANCE",
+    "SELECT_MAX_CONDUCTANCE", "STAGES",
 ]
 
 STAGES = ("crossover", "mutation", "evaluate", "select")
