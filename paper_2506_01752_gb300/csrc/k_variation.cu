@@ -591,15 +591,16 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                 // asynchronous copies (all in flight at once), then read from
                 // shared memory. Every label occurring more than deg / 4 times
                 // ends with a positive counter.
-                int c0 = 0, c1 = 0, c2 = 0, n0 = 0, n1 = 0, n2 = 0;
+                // Empty slots keep distinct negative labels until first filled;
+                // an empty slot that still holds x takes it back (the same state
+                // as filling a free slot, since no label is ever in two slots).
+                int c0 = -1, c1 = -2, c2 = -3, n0 = 0, n1 = 0, n2 = 0;
                 auto mg = [&](int x, bool ok) {
-                    // Branch-free update (lanes disagree on the case): match -> +1;
-                    // else the first empty slot takes x; else every counter -1.
-                    const bool m0 = x == c0, m1 = !m0 && x == c1, m2 = !m0 && !m1 && x == c2;
-                    const bool miss = !(m0 || m1 || m2);
-                    const bool f0 = miss && n0 == 0, f1 = miss && !f0 && n1 == 0;
-                    const bool f2 = miss && !f0 && !f1 && n2 == 0;
-                    const int dec = (ok && miss && !f0 && !f1 && !f2) ? 1 : 0;
+                    const bool m0 = x == c0, m1 = x == c1, m2 = x == c2;
+                    const bool hit = m0 || m1 || m2;
+                    const bool e0 = n0 == 0, e1 = n1 == 0, e2 = n2 == 0;
+                    const bool f0 = !hit && e0, f1 = !hit && !e0 && e1, f2 = !hit && !e0 && !e1 && e2;
+                    const int dec = (ok && !hit && !e0 && !e1 && !e2) ? 1 : 0;
                     n0 = ok && (m0 || f0) ? n0 + 1 : n0 - dec;
                     n1 = ok && (m1 || f1) ? n1 + 1 : n1 - dec;
                     n2 = ok && (m2 || f2) ? n2 + 1 : n2 - dec;
