@@ -635,14 +635,16 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                     }
                 }
                 // Pass 2: exact counts of the surviving candidates.
-                const bool v0 = n0 > 0, v1 = n1 > 0, v2 = n2 > 0;
+                // Live candidates; an empty counter gets a label no neighbour
+                // (nor the -1 padding below) can have, so it counts 0.
+                const int s0 = n0 > 0 ? c0 : -2, s1 = n1 > 0 ? c1 : -3, s2 = n2 > 0 ? c2 : -4;
                 int h0 = 0, h1 = 0, h2 = 0;
                 if (has && deg <= kTileRows) {
                     for (int j = 0; j < deg; ++j) {
                         const int x = tile[j * kTileStride + lane];
-                        h0 += v0 && x == c0;
-                        h1 += v1 && x == c1;
-                        h2 += v2 && x == c2;
+                        h0 += x == s0;
+                        h1 += x == s1;
+                        h2 += x == s2;
                     }
                 }
                 if (deg > kTileRows) {
@@ -651,9 +653,9 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
 #pragma unroll 4
                         for (int j = 0; j < kTileRows; ++j) {
                             const int x = tile[j * kTileStride + lane];
-                            h0 += v0 && x == c0;
-                            h1 += v1 && x == c1;
-                            h2 += v2 && x == c2;
+                            h0 += x == s0;
+                            h1 += x == s1;
+                            h2 += x == s2;
                         }
                     }
                     for (int e0 = kTileRows; e0 < deg; e0 += 32) {
@@ -668,9 +670,9 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                             }
 #pragma unroll
                             for (int t = 0; t < 8; ++t) {
-                                h0 += v0 && xs[t] == c0;
-                                h1 += v1 && xs[t] == c1;
-                                h2 += v2 && xs[t] == c2;
+                                h0 += xs[t] == s0;
+                                h1 += xs[t] == s1;
+                                h2 += xs[t] == s2;
                             }
                         }
                     }
@@ -681,9 +683,9 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                 const bool done = has && 4 * best > deg;
                 if (done) {
                     // Tied candidates in ascending order, then the MTIE pick.
-                    int a = v0 && h0 == best ? c0 : INT_MAX;
-                    int b = v1 && h1 == best ? c1 : INT_MAX;
-                    int c = v2 && h2 == best ? c2 : INT_MAX;
+                    int a = h0 == best ? s0 : INT_MAX;
+                    int b = h1 == best ? s1 : INT_MAX;
+                    int c = h2 == best ? s2 : INT_MAX;
                     int lo = min(a, b), hi = max(a, b);
                     a = lo; b = hi;
                     lo = min(b, c); hi = max(b, c);
