@@ -56,7 +56,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--requests", type=int, default=80, help="serving trace length (--workload serve)")
     ap.add_argument("--hbm-budget-gb", type=int, default=64, help="server device-memory budget")
-    ap.add_argument("--max-running", type=int, default=8, help="server concurrency limit")
+    ap.add_argument("--max-running", type=int, default=4, help="server concurrency limit")
+    ap.add_argument("--depth", type=int, default=8, help="server: generations issued ahead per running job")
     ap.add_argument("--policy", type=int, default=0, help="server admission: 0 FIFO, 1 shortest work first")
     ap.add_argument("--preroll-s", type=float, default=0.5,
                     help="seconds of extra untimed generations before timing (clock settling)")
@@ -561,7 +562,7 @@ def run_serve(args):
     mocd.destroy(h)
 
     # Continuous-batching server (background scheduler + admission workers).
-    srv = mocd.Server(args.hbm_budget_gb << 30, max_running=args.max_running, depth=8)
+    srv = mocd.Server(args.hbm_budget_gb << 30, max_running=args.max_running, depth=args.depth)
     srv.start(admission_threads=2, policy=args.policy)
     t0 = time.perf_counter()
     ids, done_at, submitted = [], {}, 0
@@ -604,7 +605,7 @@ def run_serve(args):
         "failed": failed, "requests": n_req, "rate_per_s": rate, "generations": G,
         "config": {"workload": "Poisson 20/s; LFR-style graphs, n log-spaced 1e3-1e6 (12-graph pool), "
                                "mu U[0.1,0.6]; N_p=100, G=100",
-                   "hbm_budget_gb": args.hbm_budget_gb, "max_running": args.max_running, "depth": 8,
+                   "hbm_budget_gb": args.hbm_budget_gb, "max_running": args.max_running, "depth": args.depth,
                    "admission": "shortest work first" if args.policy else "first come first served",
                    "admission_threads": 2,
                    "pool": [d for _, _, d in pool]},
