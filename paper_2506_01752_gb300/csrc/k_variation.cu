@@ -581,19 +581,17 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
             bool have_tw = false;
             uint4 tw = make_uint4(0, 0, 0, 0);
             for (int base = 0; base < nsel; base += 32) {
-                // Lane = pair. A label held by more than deg / 2 neighbours is the
-                // unique most frequent one: find the Boyer-Moore candidate, then
-                // count it.
+                // Lane = pair (selected child i of node v).
                 const bool has = base + lane < nsel;
                 const int i = has ? s_list[base + lane] : 0;
                 // Pass 1: Misra-Gries summary with three counters. The labels of
                 // the first kTileRows neighbours are staged into the tile with
                 // asynchronous copies (all in flight at once), then read from
                 // shared memory. Every label occurring more than deg / 4 times
-                // ends with a positive counter.
-                // Empty slots keep distinct negative labels until first filled;
-                // an empty slot that still holds x takes it back (the same state
-                // as filling a free slot, since no label is ever in two slots).
+                // ends with a positive counter. Empty counters keep distinct
+                // negative labels until first filled; an empty counter that still
+                // holds x takes it back (the same summary as filling a free one,
+                // since no label is ever held by two counters).
                 int c0 = -1, c1 = -2, c2 = -3, n0 = 0, n1 = 0, n2 = 0;
                 auto mg = [&](int x, bool ok) {
                     const bool m0 = x == c0, m1 = x == c1, m2 = x == c2;
