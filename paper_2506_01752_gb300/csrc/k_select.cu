@@ -51,31 +51,38 @@ struct SelShared {
     unsigned long long wscan[kSelWarps];
     int fsize[kMaxPoints + 1];
     int keep[kMaxPop];
+    unsigned long long xa[2][kMaxPoints], xb[2][kMaxPoints];  // sort exchange, double-buffered
 };
 
-// Bitonic sort, ascending, of one key per thread over the first `size`
-// threads (a power of two, 32..kSelThreads); the other threads only join the
-// barriers. The compare-exchange is branch-free.
-__device__ __forceinline__ Key block_sort(SelShared &S, Key key, int size)
+// Bitonic sort, ascending, of one key per thread over the first SIZE threads
+// (a power of two, 32..kSelThreads); the other threads only join the
+// barriers. Fully unrolled: distances below 32 exchange by shuffles, larger
+// ones through shared memory. The compare-exchange is branch-free.
+template <int SIZE>
+__device__ __forceinline__ Key block_sort_fixed(SelShared &S, Key key)
 {
     const int t = threadIdx.x;
-    const bool in = t < size;
-#pragma unroll 1
-    for (int k = 2; k <= size; k <<= 1) {
-#pragma unroll 1
+    const bool in = t < SIZE;
+    int buf = 0;  // exchange buffer of the next shared-memory stage
+#pragma unroll
+    for (int k = 2; k <= SIZE; k <<= 1) {
+#pragma unroll
         for (int j = k >> 1; j > 0; j >>= 1) {
             Key other;
             if (j >= 32) {
+                // Consecutive shared-memory stages alternate buffers, so the
+                // barrier of one stage also orders the previous stage's reads
+                // before the next write of the same buffer.
                 if (in) {
-                    S.sa[t] = key.a;
-                    S.sb[t] = key.b;
+                    S.xa[buf][t] = key.a;
+                    S.xb[buf][t] = key.b;
                 }
                 __syncthreads();
                 if (in) {
-                    other.a = S.sa[t ^ j];
-                    other.b = S.sb[t ^ j];
+                    other.a = S.xa[buf][t ^ j];
+                    other.b = S.xb[buf][t ^ j];
                 }
-                __syncthreads();
+                buf ^= 1;
             } else if (in) {
                 other.a = __shfl_xor_sync(kFull, key.a, j);
                 other.b = __shfl_xor_sync(kFull, key.b, j);
@@ -89,7 +96,20 @@ __device__ __forceinline__ Key block_sort(SelShared &S, Key key, int size)
             }
         }
     }
+    __syncthreads();  // the last exchange's reads precede any later use of the buffers
     return key;
+}
+
+// The sort above for size = 32, 64, 128 or 256 (the power of two covering
+// the points).
+__device__ __noinline__ Key block_sort(SelShared &S, Key key, int size)
+{
+    switch (size) {
+    case 32: return block_sort_fixed<32>(S, key);
+    case 64: return block_sort_fixed<64>(S, key);
+    case 128: return block_sort_fixed<128>(S, key);
+    default: return block_sort_fixed<kSelThreads>(S, key);
+    }
 }
 
 // Inclusive block-wide scans over thread order (min of u64, max of int).
@@ -104,7 +124,8 @@ __device__ unsigned long long block_min_scan(SelShared &S, unsigned long long v)
     if (lane == 31) S.wscan[w] = v;
     __syncthreads();
     unsigned long long pre = kInf64;
-    for (int q = 0; q < w; ++q) pre = min(pre, S.wscan[q]);
+#pragma unroll
+    for (int q = 0; q < kSelWarps; ++q) pre = q < w ? min(pre, S.wscan[q]) : pre;
     __syncthreads();
     return min(v, pre);
 }
@@ -120,7 +141,8 @@ __device__ int block_max_scan(SelShared &S, int v)
     if (lane == 31) S.wscan[w] = (unsigned long long)(unsigned)v;
     __syncthreads();
     int pre = 0;
-    for (int q = 0; q < w; ++q) pre = max(pre, (int)(unsigned)S.wscan[q]);
+#pragma unroll
+    for (int q = 0; q < kSelWarps; ++q) pre = q < w ? max(pre, (int)(unsigned)S.wscan[q]) : pre;
     __syncthreads();
     return max(v, pre);
 }
