@@ -6,7 +6,8 @@ evaluation of both objectives, environmental selection) for all N_p children,
 on the LFR-style graph of the paper's scalability setup (n = 40,000, average
 degree 20, maximum 50, tau1 = 2, tau2 = 1, communities 20-100, mu = 0.3),
 N_p = 100, E_S = 4, C_P = 0.8, M_P = 0.2. The metric is N_p * m edge-evals per
-generation divided by the device time of the generation.
+generation divided by the device time of the generation; the K timed steps are
+generations 1..K of a fresh run, after a separate warm-up run.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
     python bench.py --workload batch64|serve|quality   (batched jobs, serving,
@@ -324,6 +325,11 @@ def run_mine(args):
         mocd.synchronize(ctx)
         pre += 20
     mocd.synchronize(ctx)
+    # The timed steps are generations 1..K of a fresh run (the configuration's
+    # G-generation job), not a population that the warm-up has already
+    # converged: re-initialising puts the run back to generation 0.
+    mocd.population_init(ctx, params)
+    mocd.synchronize(ctx)
     barrier(world)
     torch.cuda.synchronize()
 
@@ -410,7 +416,8 @@ def run_mine(args):
                        "step": "one generation of Alg. 1 (crossover, mutation, evaluation, selection)",
                        "l2": f"flushed between timed steps ({FLUSH_BYTES >> 20} MB write, outside the events)",
                        "parallelism": f"{world} independent replica(s)",
-                       "warmup_generations": args.warmup + pre},
+                       "warmup_generations": args.warmup + pre,
+                       "timed_generations": f"1-{args.steps} of a fresh run (population re-initialised after the warm-up)"},
             "roofline": roofline,
             "roofline_objective": roofline_objective,
             "cpu_baseline": cpu,

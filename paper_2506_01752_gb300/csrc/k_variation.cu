@@ -328,23 +328,58 @@ crossover_kernel(GenParams gp, const int32_t *buf0, const int32_t *buf1, int32_t
 // three-counter Misra-Gries pass and recounts the survivors exactly, which
 // settles the pair whenever the best count c has 4 c > deg. The other pairs
 // get an exact vote by the whole warp: degree <= 32, one neighbour per lane
-// grouped by __match_any_sync; 33..64, a sorting network over two labels per
+// grouped by __match_any_sync, two pairs at a time, the pick(u, t)-th tied
+// label found by removing minima (shallow ranks) or by sorting the tied
+// labels across the warp (deep ranks: the first generations, when labels are
+// still nearly all distinct); 33..64, a sorting network over two labels per
 // lane; beyond, a count table in shared memory.
 // ---------------------------------------------------------------------------
 
-// The k-th smallest of the distinct labels held by the lanes of `cand`: the
-// minimum is removed k times (labels are non-negative).
-__device__ __forceinline__ int select_kth_lane(unsigned cand, int x, unsigned k)
+// The ka-th and kb-th smallest of the distinct labels held by the lanes of
+// two candidate sets ca and cb, by removing the minimum k times; the two
+// chains run side by side so that their reductions overlap. la / lb receive
+// the lanes (-1 for an empty set). Labels are non-negative.
+__device__ __forceinline__ void select_kth_lane2(unsigned ca, int xa, unsigned ka, unsigned cb, int xb, unsigned kb,
+                                                 int &la, int &lb)
 {
-    unsigned act = cand;
     const int lane = threadIdx.x & 31;
-    for (unsigned s = 0; s < k; ++s) {
-        const unsigned mn = __reduce_min_sync(kFull, ((act >> lane) & 1u) ? (unsigned)x : 0xffffffffu);
-        act &= ~__ballot_sync(kFull, ((act >> lane) & 1u) && (unsigned)x == mn);
+    unsigned acta = ca, actb = cb;
+    const unsigned kmax = ka > kb ? ka : kb;
+    for (unsigned s = 0; s < kmax; ++s) {
+        const unsigned mna = __reduce_min_sync(kFull, ((acta >> lane) & 1u) ? (unsigned)xa : 0xffffffffu);
+        const unsigned mnb = __reduce_min_sync(kFull, ((actb >> lane) & 1u) ? (unsigned)xb : 0xffffffffu);
+        const unsigned ra = __ballot_sync(kFull, ((acta >> lane) & 1u) && (unsigned)xa == mna);
+        const unsigned rb = __ballot_sync(kFull, ((actb >> lane) & 1u) && (unsigned)xb == mnb);
+        if (s < ka) acta &= ~ra;
+        if (s < kb) actb &= ~rb;
     }
-    const unsigned mn = __reduce_min_sync(kFull, ((act >> lane) & 1u) ? (unsigned)x : 0xffffffffu);
-    return __ffs(__ballot_sync(kFull, ((act >> lane) & 1u) && (unsigned)x == mn)) - 1;
+    const unsigned mna = __reduce_min_sync(kFull, ((acta >> lane) & 1u) ? (unsigned)xa : 0xffffffffu);
+    const unsigned mnb = __reduce_min_sync(kFull, ((actb >> lane) & 1u) ? (unsigned)xb : 0xffffffffu);
+    la = __ffs(__ballot_sync(kFull, ((acta >> lane) & 1u) && (unsigned)xa == mna)) - 1;
+    lb = __ffs(__ballot_sync(kFull, ((actb >> lane) & 1u) && (unsigned)xb == mnb)) - 1;
 }
+
+// Two ascending bitonic sorts across the warp (one value per lane each),
+// run as independent chains.
+__device__ __forceinline__ void warp_sort32x2(unsigned &a, unsigned &b)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const unsigned pa = __shfl_xor_sync(kFull, a, j);
+            const unsigned pb = __shfl_xor_sync(kFull, b, j);
+            const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+            a = keep_min ? min(a, pa) : max(a, pa);
+            b = keep_min ? min(b, pb) : max(b, pb);
+        }
+    }
+}
+
+// Above this tie rank the k-th tied label comes from sorting the tied labels
+// rather than from removing the minimum k times.
+constexpr unsigned kRemovalMax = 4;
 
 // MTIE words of the lane's four children at node v (computed by every lane
 // together, the first time a tie occurs at v).
@@ -437,19 +472,24 @@ __device__ __forceinline__ int warp_mode_sort64(const GenParams &gp, const int32
     return __shfl_sync(kFull, b, __ffs(w) - 1);
 }
 
-// Exact neighbour-majority of one pair of a node with degree > 32 by the
-// whole warp: 33..64 by the sorting network above; beyond that a per-warp
-// open-addressing count table in shared memory (inserts aggregated per
-// distinct label of a 32-neighbour chunk with __match_any_sync), then the
-// largest count, the tied labels and the pick(u, t)-th smallest of them.
-__device__ __forceinline__ int warp_mode(const GenParams &gp, const int32_t *__restrict__ child,
-                                         const int32_t *__restrict__ col_idx, int beg, int deg,
-                                         const int *tile_col, int i, int *hkey, int *hcnt, int hbits,
-                                         uint32_t tie_u)
+// Exact neighbour-majority of one pair of a node with degree > 64 by the
+// whole warp: a per-warp open-addressing
+// count table in shared memory, sized to the node (the
+// smallest power of two with at least 2 deg slots), filled with one insert
+// per distinct label of each 32-neighbour chunk (__match_any_sync gives the
+// multiplicity). The labels reaching the largest count are then compacted
+// (one slot per distinct label) and the pick(u, t)-th smallest of them is
+// found either by stepping up through the minima (shallow ranks) or bit by
+// bit from the top (deep ranks).
+__device__ __forceinline__ int warp_mode_table(const GenParams &gp, const int32_t *__restrict__ child,
+                                            const int32_t *__restrict__ col_idx, int beg, int deg,
+                                            const int *tile_col, int i, int *hkey, int *hcnt, uint32_t tie_u)
 {
     const int lane = threadIdx.x & 31;
     const int W = gp.W;
-    if (deg <= 64) return warp_mode_sort64(gp, child, col_idx, beg, deg, tile_col, i, tie_u);
+    // 2 deg <= 2 dmax <= the per-warp capacity, so the table fits.
+    int hbits = 7;
+    while ((1 << hbits) < 2 * deg) ++hbits;
     const int HS = 1 << hbits;
     const int per_lane = HS >> 5;
     for (int e = lane; e < HS; e += 32) {
@@ -467,7 +507,7 @@ __device__ __forceinline__ int warp_mode(const GenParams &gp, const int32_t *__r
         const unsigned peers = __match_any_sync(kFull, x);
         if (in && (peers & ((1u << lane) - 1u)) == 0) {
             uint32_t h = hash_slot(x, hbits);
-            // The table holds at most deg < HS / 2 distinct labels, so an empty
+            // The table holds at most deg <= HS / 2 distinct labels, so an empty
             // or matching slot is always found.
             for (int probe = 0; probe < HS; ++probe) {
                 const int prev = atomicCAS(hkey + h, -1, x);
@@ -486,21 +526,58 @@ __device__ __forceinline__ int warp_mode(const GenParams &gp, const int32_t *__r
     unsigned act = 0;
     for (int s = 0; s < per_lane; ++s)
         if ((unsigned)hcnt[lane + 32 * s] == mx) act |= 1u << s;
-    const unsigned t = __reduce_add_sync(kFull, (unsigned)__popc(act));
-    const unsigned kk = t > 1 ? pick_index(tie_u, t) : 0u;
-    // Remove the smallest tied label kk times; the next smallest wins.
-    unsigned mn = 0;
-    for (unsigned s = 0; s <= kk; ++s) {
-        unsigned my = 0xffffffffu;
-        for (int e = 0; e < per_lane; ++e)
-            if ((act >> e) & 1u) my = min(my, (unsigned)hkey[lane + 32 * e]);
-        mn = __reduce_min_sync(kFull, my);
-        if (s < kk)
-            for (int e = 0; e < per_lane; ++e)
-                if (((act >> e) & 1u) && (unsigned)hkey[lane + 32 * e] == mn) act &= ~(1u << e);
+    // Compact the tied labels into hcnt[0, t) (the counts are no longer needed).
+    const unsigned mine = (unsigned)__popc(act);
+    unsigned incl = mine;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned y = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += y;
+    }
+    const int t = (int)__shfl_sync(kFull, incl, 31);
+    int at = (int)(incl - mine);
+    __syncwarp();
+    for (int s = 0; s < per_lane; ++s)
+        if ((act >> s) & 1u) hcnt[at++] = hkey[lane + 32 * s];
+    __syncwarp();
+    const unsigned kk = t > 1 ? pick_index(tie_u, (uint32_t)t) : 0u;
+    int res;
+    if (kk > (unsigned)gp.label_bits) {
+        // Deep rank: at bit b (from the top), count the tied labels that agree
+        // with the bits chosen so far and have a 0 there; the rank falls among
+        // them or, past them, among those with a 1. Labels are below
+        // 2^label_bits.
+        unsigned prefix = 0, rank = kk;
+        for (int b = gp.label_bits - 1; b >= 0; --b) {
+            const unsigned above = ~((2u << b) - 1u);  // the bits above b
+            unsigned c = 0;
+            for (int e = lane; e < t; e += 32) {
+                const unsigned key = (unsigned)hcnt[e];
+                c += ((key & above) == prefix && ((key >> b) & 1u) == 0u) ? 1u : 0u;
+            }
+            const unsigned cnt = __reduce_add_sync(kFull, c);
+            if (rank >= cnt) {
+                rank -= cnt;
+                prefix |= 1u << b;
+            }
+        }
+        res = (int)prefix;
+    } else {
+        // Shallow rank: the smallest tied label, then kk times the smallest
+        // one above the previous (the tied labels are distinct, >= 0).
+        int last = -1;
+        for (unsigned s = 0; s <= kk; ++s) {
+            unsigned my = 0xffffffffu;
+            for (int e = lane; e < t; e += 32) {
+                const int key = hcnt[e];
+                if (key > last) my = min(my, (unsigned)key);
+            }
+            last = (int)__reduce_min_sync(kFull, my);
+        }
+        res = last;
     }
     __syncwarp();
-    return (int)mn;
+    return res;
 }
 
 __global__ void __launch_bounds__(kMutBlock, 8)
@@ -516,7 +593,6 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int HS = gp.hash_size;
-    const int hbits = HS > 0 ? __ffs(HS) - 1 : 0;
     int *s_list = smem + wib * (2 * kMaxPop + kTileRows * kTileStride + 2 * HS);  // selected children
     int *s_res = s_list + kMaxPop;              // by child index: v's own label, then the result
     int *tile = s_res + kMaxPop;                // [kTileRows][kTileStride]: label of neighbour j, pair lane
@@ -732,11 +808,25 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                         const uint32_t ua = __shfl_sync(kFull, word_of(tw, ia & 3), ia >> 2);
                         const uint32_t ub = __shfl_sync(kFull, word_of(tw, ib & 3), ib >> 2);
                         const int ta = __popc(da), tb = __popc(db);
-                        const int sa = ta == 1 ? __ffs(da) - 1 : select_kth_lane(da, xa, pick_index(ua, (uint32_t)ta));
-                        int sb = 0;
-                        if (two) sb = tb == 1 ? __ffs(db) - 1 : select_kth_lane(db, xb, pick_index(ub, (uint32_t)tb));
-                        const int ra = __shfl_sync(kFull, xa, sa);
-                        const int rb = __shfl_sync(kFull, xb, sb);
+                        const unsigned ka = ta > 1 ? pick_index(ua, (uint32_t)ta) : 0u;
+                        const unsigned kb = (two && tb > 1) ? pick_index(ub, (uint32_t)tb) : 0u;
+                        int ra, rb;
+                        if (ka > kRemovalMax || kb > kRemovalMax) {
+                            // The tied labels are distinct (one leader per label):
+                            // sorted ascending, with the other lanes last, the
+                            // k-th tied label sits in lane k.
+                            unsigned va = ((da >> lane) & 1u) ? (unsigned)xa : 0xffffffffu;
+                            unsigned vb = (two && ((db >> lane) & 1u)) ? (unsigned)xb : 0xffffffffu;
+                            warp_sort32x2(va, vb);
+                            ra = (int)__shfl_sync(kFull, va, (int)ka);
+                            rb = (int)__shfl_sync(kFull, vb, (int)kb);
+                        } else {
+                            int sa = __ffs(da) - 1, sb = __ffs(db) - 1;
+                            if (ta > 1 || (two && tb > 1)) select_kth_lane2(da, xa, ka, two ? db : 0u, xb, kb, sa, sb);
+                            if (!two) sb = 0;
+                            ra = __shfl_sync(kFull, xa, sa);
+                            rb = __shfl_sync(kFull, xb, sb);
+                        }
                         if (lane == 0) {
                             s_res[ia] = ra;
                             if (two) s_res[ib] = rb;
@@ -748,7 +838,9 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                     rest &= rest - 1;
                     const int ic = __shfl_sync(kFull, i, l);
                     const uint32_t u = __shfl_sync(kFull, word_of(tw, ic & 3), ic >> 2);
-                    const int lab = warp_mode(gp, child, col_idx, beg, deg, tile + l, ic, hkey, hcnt, hbits, u);
+                    const int lab = deg <= 64
+                                        ? warp_mode_sort64(gp, child, col_idx, beg, deg, tile + l, ic, u)
+                                        : warp_mode_table(gp, child, col_idx, beg, deg, tile + l, ic, hkey, hcnt, u);
                     if (lane == 0) s_res[ic] = lab;
                 }
                 __syncwarp();
