@@ -327,12 +327,15 @@ crossover_kernel(GenParams gp, const int32_t *buf0, const int32_t *buf1, int32_t
 // selected children. Each lane summarises its pair's neighbour labels with a
 // three-counter Misra-Gries pass and recounts the survivors exactly, which
 // settles the pair whenever the best count c has 4 c > deg. The other pairs
-// get an exact vote by the whole warp: degree <= 32, one neighbour per lane
-// grouped by __match_any_sync, two pairs at a time, the pick(u, t)-th tied
-// label found by removing minima (shallow ranks) or by sorting the tied
-// labels across the warp (deep ranks: the first generations, when labels are
-// still nearly all distinct); 33..64, a sorting network over two labels per
-// lane; beyond, a count table in shared memory.
+// get an exact vote. Degree <= 32: when many pairs of the node are left (the
+// first generations, while the labels are still nearly all distinct), each
+// lane sorts its own pair's labels in registers with an odd-even merge
+// network of 8, 16 or 32 entries and reads the tied labels off the runs;
+// when few are left, the whole warp votes on two pairs at a time (one
+// neighbour per lane grouped by __match_any_sync, the pick(u, t)-th tied
+// label by removing minima or, for deep ranks, by sorting the tied labels
+// across the warp). Degree 33..64: a sorting network over two labels per
+// lane. Beyond: a count table in shared memory.
 // ---------------------------------------------------------------------------
 
 // The ka-th and kb-th smallest of the distinct labels held by the lanes of
@@ -409,6 +412,128 @@ __device__ __forceinline__ void cp_async_wait_all()
 constexpr int kTileStride = 33;  // padded row of the per-warp label tile
 constexpr int kTileRows = 32;    // neighbours whose labels the tile keeps
 constexpr int kMutBlock = 128;   // mutation threads per block (shared memory bound)
+
+// Batcher's odd-even merge sort of x[0, N) (N a power of two), ascending,
+// written as compile-time recursion so that every index is a constant and
+// the array stays in registers.
+template <int A, int B>
+__device__ __forceinline__ void cmp_exchange(int *x)
+{
+    const int lo = min(x[A], x[B]);
+    const int hi = max(x[A], x[B]);
+    x[A] = lo;
+    x[B] = hi;
+}
+
+// Compare-exchanges (i, i + R) for i = I, I + 2R, ... while i + R < END.
+template <int I, int R, int END>
+struct CmpRun {
+    static __device__ __forceinline__ void run(int *x)
+    {
+        if constexpr (I + R < END) {
+            cmp_exchange<I, I + R>(x);
+            CmpRun<I + 2 * R, R, END>::run(x);
+        }
+    }
+};
+
+// Merge of the two sorted halves of x[LO, LO + N), elements R apart.
+template <int LO, int N, int R>
+struct OddEvenMerge {
+    static __device__ __forceinline__ void run(int *x)
+    {
+        if constexpr (2 * R < N) {
+            OddEvenMerge<LO, N, 2 * R>::run(x);
+            OddEvenMerge<LO + R, N, 2 * R>::run(x);
+            CmpRun<LO + R, R, LO + N>::run(x);
+        } else {
+            cmp_exchange<LO, LO + R>(x);
+        }
+    }
+};
+
+// Sort of x[LO, HI] (inclusive).
+template <int LO, int HI>
+struct OddEvenSort {
+    static __device__ __forceinline__ void run(int *x)
+    {
+        if constexpr (HI > LO) {
+            constexpr int MID = LO + (HI - LO) / 2;
+            OddEvenSort<LO, MID>::run(x);
+            OddEvenSort<MID + 1, HI>::run(x);
+            OddEvenMerge<LO, HI - LO + 1, 1>::run(x);
+        }
+    }
+};
+
+template <int N>
+__device__ __forceinline__ void sort_network(int (&x)[N])
+{
+    OddEvenSort<0, N - 1>::run(x);
+}
+
+// Exact neighbour-majority of one pair by its own lane: the pair's deg <= N
+// labels (column `col` of the staged tile) are sorted in registers; equal
+// labels then form runs, the longest runs are the tied labels in ascending
+// order, and the pick(u, t)-th of them is the result.
+template <int N>
+__device__ __forceinline__ int lane_mode(const int *col, int deg, uint32_t u)
+{
+    int x[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) x[j] = j < deg ? col[j * kTileStride] : INT_MAX;
+    sort_network<N>(x);
+    // One pass: the longest run length among the deg real entries and the
+    // mask of the positions where a run of that length ends.
+    int run = 0, best = 0;
+    unsigned ends = 0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        run = (j > 0 && x[j] == x[j - 1]) ? run + 1 : 1;
+        const bool last = j < deg && (j + 1 == deg || (j + 1 < N && x[j + 1] != x[j]));
+        if (last && run > best) {
+            best = run;
+            ends = 0;
+        }
+        if (last && run == best) ends |= 1u << j;
+    }
+    const int t = __popc(ends);
+    const unsigned kk = t > 1 ? pick_index(u, (uint32_t)t) : 0u;
+    // Position of the kk-th set bit of `ends`, halving the window each step.
+    unsigned m = ends, k = kk;
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const unsigned low = m & ((1u << w) - 1u);
+        const unsigned c = (unsigned)__popc(low);
+        if (k >= c) {
+            k -= c;
+            m >>= w;
+            pos += w;
+        } else {
+            m = low;
+        }
+    }
+    int res = x[0];
+#pragma unroll
+    for (int j = 1; j < N; ++j) res = pos == j ? x[j] : res;
+    return res;
+}
+
+// Lane-parallel exact vote of every unresolved pair of a node with
+// deg <= kTileRows; unresolved lanes write their result.
+template <int N>
+__device__ __forceinline__ void lane_votes(const int *tile, int deg, bool mine, int i, uint4 tw, int *s_res)
+{
+    const int src = i >> 2;
+    const uint32_t w0 = __shfl_sync(0xffffffffu, tw.x, src);
+    const uint32_t w1 = __shfl_sync(0xffffffffu, tw.y, src);
+    const uint32_t w2 = __shfl_sync(0xffffffffu, tw.z, src);
+    const uint32_t w3 = __shfl_sync(0xffffffffu, tw.w, src);
+    const int k = i & 3;
+    const uint32_t u = k == 0 ? w0 : (k == 1 ? w1 : (k == 2 ? w2 : w3));
+    if (mine) s_res[i] = lane_mode<N>(tile + (threadIdx.x & 31), deg, u);
+}
 
 // Exact neighbour-majority of one pair whose node has 32 < deg <= 64: the
 // labels (two per lane: neighbour j = lane from the tile, 32 + lane from
@@ -580,7 +705,7 @@ __device__ __forceinline__ int warp_mode_table(const GenParams &gp, const int32_
     return res;
 }
 
-__global__ void __launch_bounds__(kMutBlock, 8)
+__global__ void __launch_bounds__(kMutBlock, 6)
 mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
                 const int32_t *__restrict__ order, const int32_t *__restrict__ child, int32_t *__restrict__ q,
                 const uint32_t *__restrict__ gen_ptr, uint32_t *__restrict__ hist,
@@ -782,6 +907,22 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                     have_tw = true;
                 }
                 if (deg <= kTileRows) {
+                    // Many unresolved pairs: every lane settles its own pair
+                    // with a sorting network (all pairs at once).
+                    const int nrest = __popc(rest);
+                    const bool mine = (rest >> lane) & 1u;
+                    if (deg <= 8 && nrest >= 2) {
+                        lane_votes<8>(tile, deg, mine, i, tw, s_res);
+                        rest = 0;
+                    } else if (deg > 8 && deg <= 16 && nrest >= 5) {
+                        lane_votes<16>(tile, deg, mine, i, tw, s_res);
+                        rest = 0;
+                    } else if (deg > 16 && nrest >= 10) {
+                        lane_votes<32>(tile, deg, mine, i, tw, s_res);
+                        rest = 0;
+                    }
+                }
+                if (deg <= kTileRows) {
                     // Exact vote by the whole warp (lane = neighbour), two
                     // unresolved pairs at a time as independent chains.
                     const unsigned lt = (1u << lane) - 1u;
@@ -846,10 +987,8 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                 __syncwarp();
             }
             __syncwarp();
-            if (sel & 1u) out.x = s_res[4 * lane + 0];
-            if (sel & 2u) out.y = s_res[4 * lane + 1];
-            if (sel & 4u) out.z = s_res[4 * lane + 2];
-            if (sel & 8u) out.w = s_res[4 * lane + 3];
+            // s_res holds the unselected children's labels and the results.
+            if (active) out = reinterpret_cast<const int4 *>(s_res)[lane];
             __syncwarp();
         }
         if (active) Q4[(size_t)v * nq + lane] = out;
