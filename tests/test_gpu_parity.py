@@ -56,6 +56,20 @@ def hub_of_degree(d, extra=300, seed=0):
                                 np.concatenate([np.arange(1, n), b]))
 
 
+def degree_ladder(degrees=(1, 2, 7, 8, 9, 15, 16, 17, 31, 32, 33, 63, 64, 65, 127, 128, 129)):
+    """Disjoint stars whose centres have the given degrees: the boundaries of
+    the mutation vote's per-lane sorting networks (8, 16, 32 entries), of the
+    warp sort (33..64) and of the count table (65 and up). With random labels
+    every neighbour label of a centre is distinct, so its votes tie widely
+    (deep tie ranks)."""
+    u, v, base = [], [], 0
+    for d in degrees:
+        u += [base] * d
+        v += list(range(base + 1, base + 1 + d))
+        base += d + 1
+    return synth.csr_from_edges(base, u, v)
+
+
 def complete_graph(k):
     u, v = np.triu_indices(k, 1)
     return synth.csr_from_edges(k, u, v)
@@ -195,6 +209,8 @@ def test_generations_match_oracle(gname, G, kw):
     ("one-edge", 3, dict(pop_size=20, p_mutation=1.0)),     # thousands of isolated nodes
     ("k40", 4, dict(pop_size=30, p_mutation=0.5)),          # one dense community, degree 39
     ("k33", 3, dict(pop_size=16, p_mutation=1.0)),          # degree exactly 32
+    ("ladder", 3, dict(pop_size=40, p_mutation=1.0)),      # network-size boundaries, two rounds of pairs
+    ("ladder", 4, dict(pop_size=100, seed=9)),
     ("lfr-3k", 2, dict(pop_size=50, seed=0xDEADBEEF12345678)),  # both key words non-zero
 ])
 def test_extreme_graphs_match_oracle(gname, G, kw):
@@ -203,6 +219,7 @@ def test_extreme_graphs_match_oracle(gname, G, kw):
         "one-edge": lambda: synth.csr_from_edges(3000, [17], [2950]),
         "k40": lambda: complete_graph(40),
         "k33": lambda: complete_graph(33),
+        "ladder": degree_ladder,
         "lfr-3k": GRAPHS["lfr-3k"],
     }[gname]()
     gp, op = _params(**kw)
