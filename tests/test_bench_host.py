@@ -55,6 +55,28 @@ def test_algorithmic_bytes():
     assert b["mutation"] == 8 * 100 * 1000 + 4 * 0.2 * 100 * 10000 + csr + 4 * 100 * 1000
 
 
+def test_recorded_traffic_only_for_the_current_source(tmp_path, monkeypatch):
+    """A profile's DRAM traffic line counts only while the kernel source it
+    was captured on is unchanged (matched by the source hash); otherwise the
+    bench reports null traffic."""
+    sys.path.insert(0, ROOT)
+    import bench
+    src = tmp_path / "paper_2506_01752_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "k_eval.cu").write_text("// version 1\n")
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    digest = bench.source_digest("evaluate")
+    (tmp_path / "profiles" / "evaluate_kernel_lfr-40k.md").write_text(
+        f"traffic_bytes_per_launch[evaluate@lfr-40k]: 12345 source_sha256_16: {digest}\n"
+        "traffic_bytes_per_launch[evaluate@lfr-1m]: 999 source_sha256_16: 0000000000000000\n")
+    assert bench.recorded_traffic("evaluate", "lfr-40k") == 12345.0
+    assert bench.recorded_traffic("evaluate", "lfr-1m") is None      # captured on another source
+    assert bench.recorded_traffic("mutation", "lfr-40k") is None     # no line for this kernel
+    (src / "k_eval.cu").write_text("// version 2\n")
+    assert bench.recorded_traffic("evaluate", "lfr-40k") is None     # kernel changed since
+
+
 def test_reference_arm_prints_one_line():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
                           "--workload", "planted-1k", "--steps", "3", "--warmup", "1"],
