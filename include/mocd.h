@@ -25,7 +25,9 @@
  *     f2 = S / (4 m^2), each computed as one IEEE double division. Dominance
  *     (Sec. 2.2) compares (k1, k2) exactly.
  *
- * Limits: 1 <= N_p <= 128, 1 <= E_S <= 16, n < 2^30, 2m < 2^31.
+ * Limits: 1 <= N_p <= 128, 1 <= E_S <= 16, n < 2^30, 2m < 2^31, and a
+ * maximum node degree of 512 for generations (the mutation's per-warp count
+ * table lives in shared memory); evaluation alone has no degree limit.
  */
 #ifndef MOCD_H
 #define MOCD_H
@@ -93,7 +95,8 @@ int mocd_graph_upload(mocd_ctx **out, int64_t n, const int64_t *row_ptr,
  * Create and evaluate the initial population P^(0) (Alg. 1 phases 1-2:
  * InitializePopulation, then EvaluateIndividual for each member), rank it and
  * draw the tournament of generation 1. Resets the generation counter to 0.
- * Errors: INVALID_ARG (params out of the limits above), OUT_OF_MEMORY, CUDA.
+ * Errors: INVALID_ARG (params out of the limits above, or a node of degree
+ * above 512), OUT_OF_MEMORY, CUDA.
  */
 int mocd_population_init(mocd_ctx *ctx, const mocd_params *params);
 
@@ -190,7 +193,8 @@ int mocd_get_offspring(mocd_ctx *ctx, int32_t *labels, int64_t *k1, int64_t *k2)
  *   params   as in mocd_population_init
  *   labels   host int32[N_p * n], values in [0, n)
  *   generation  number of generations already run, >= 0
- * Errors: INVALID_ARG (labels out of range), OUT_OF_MEMORY, CUDA.
+ * Errors: INVALID_ARG (labels out of range, params as in
+ * mocd_population_init, generation < 0), OUT_OF_MEMORY, CUDA.
  */
 int mocd_set_population(mocd_ctx *ctx, const mocd_params *params, const int32_t *labels,
                         int32_t generation);
