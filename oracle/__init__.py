@@ -252,6 +252,84 @@ def make_offspring(row_ptr, col_idx, params: Params, gen: int, state: State):
     return Q, qk1, qk2
 
 
+def _threads(threads):
+    if threads is None:
+        threads = min(16, os.cpu_count() or 1)
+    return max(1, int(threads))
+
+
+def make_offspring_parallel(row_ptr, col_idx, params: Params, gen: int, state: State, threads=None):
+    """As make_offspring, with the children split over host threads (the C
+    oracle releases the GIL; every child is computed by the same sequential
+    code, so the result does not depend on the thread count)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    rp, ci = _graph(row_ptr, col_idx)
+    n = rp.size - 1
+    Np = params.pop_size
+    P = np.ascontiguousarray(state.labels, dtype=np.int32)
+    k1 = np.ascontiguousarray(state.k1, dtype=np.int64)
+    k2 = np.ascontiguousarray(state.k2, dtype=np.int64)
+    Q = np.zeros((Np, n), dtype=np.int32)
+    qk1 = np.zeros(Np, dtype=np.int64)
+    qk2 = np.zeros(Np, dtype=np.int64)
+    T = min(_threads(threads), Np)
+    cuts = [Np * t // T for t in range(T + 1)]
+
+    def work(t):
+        pr = params._c()
+        return _load().orc_make_offspring_range(n, _p(rp), _p(ci), ctypes.byref(pr), gen, _p(P), _p(k1),
+                                                _p(k2), cuts[t], cuts[t + 1], _p(Q), _p(qk1), _p(qk2))
+
+    with ThreadPoolExecutor(T) as ex:
+        for rc in ex.map(work, range(T)):
+            _check(rc, "make_offspring_range")
+    return Q, qk1, qk2
+
+
+def objectives_parallel(row_ptr, col_idx, labels, threads=None):
+    """As objectives, with the labellings split over host threads."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    rp, ci = _graph(row_ptr, col_idx)
+    n = rp.size - 1
+    lab = np.ascontiguousarray(np.atleast_2d(labels), dtype=np.int32)
+    intra = np.zeros(lab.shape[0], dtype=np.int64)
+    sumsq = np.zeros(lab.shape[0], dtype=np.int64)
+
+    def work(r):
+        row = np.ascontiguousarray(lab[r])
+        a, b = np.zeros(1, np.int64), np.zeros(1, np.int64)
+        _check(_load().orc_objectives(n, _p(rp), _p(ci), _p(row), _p(a), _p(b)), "objectives")
+        intra[r], sumsq[r] = a[0], b[0]
+
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(work, range(lab.shape[0])))
+    return intra, sumsq
+
+
+def next_state(state: State, Q, qk1, qk2) -> State:
+    """EnvironmentalSelection (Alg. 1) of R = P u Q: the next P in the order
+    env_select keeps it (the step orc_run takes after the offspring)."""
+    Np = state.k1.size
+    rk1 = np.concatenate([np.asarray(state.k1, np.int64), np.asarray(qk1, np.int64)])
+    rk2 = np.concatenate([np.asarray(state.k2, np.int64), np.asarray(qk2, np.int64)])
+    keep = env_select(rk1, rk2)
+    P = np.empty_like(state.labels)
+    for k, r in enumerate(keep):
+        P[k] = state.labels[r] if r < Np else Q[r - Np]
+    return State(P, rk1[keep].copy(), rk2[keep].copy(), state.generation + 1)
+
+
+def run_parallel(row_ptr, col_idx, params: Params, state: State, generations: int, threads=None) -> State:
+    """As run, each generation's children split over host threads; the same
+    steps in the same order (offspring, then environmental selection)."""
+    for _ in range(generations):
+        Q, qk1, qk2 = make_offspring_parallel(row_ptr, col_idx, params, state.generation + 1, state, threads)
+        state = next_state(state, Q, qk1, qk2)
+    return state
+
+
 def make_offspring_range(row_ptr, col_idx, params: Params, gen: int, state: State, i0: int, i1: int):
     """Children i0 <= i < i1 of generation ``gen`` (a bounded sample of one
     generation); rows outside the range are left zero."""

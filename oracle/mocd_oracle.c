@@ -222,8 +222,11 @@ int orc_nondominated_sort(int32_t N, const int64_t *k1, const int64_t *k2, int32
     return ORC_OK;
 }
 
-/* qsort helpers: members ordered by (key, position). */
-static const int64_t *g_sort_key;
+/* qsort helpers: members ordered by (key, position). The comparators read
+ * their keys through thread-local pointers, so that several host threads may
+ * run the oracle at once (the tests split one generation's children over
+ * threads). */
+static _Thread_local const int64_t *g_sort_key;
 static int cmp_key_pos(const void *pa, const void *pb)
 {
     int32_t a = *(const int32_t *)pa, b = *(const int32_t *)pb;
@@ -267,8 +270,8 @@ int orc_crowding(int32_t N, const int64_t *k1, const int64_t *k2, const int32_t 
     return ORC_OK;
 }
 
-static const int32_t *g_rank;
-static const double *g_crowd;
+static _Thread_local const int32_t *g_rank;
+static _Thread_local const double *g_crowd;
 static int cmp_rank_crowd(const void *pa, const void *pb)
 {
     int32_t a = *(const int32_t *)pa, b = *(const int32_t *)pb;

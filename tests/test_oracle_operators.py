@@ -155,3 +155,141 @@ def test_init_sweep_two_node_path_and_isolated(oracle):
     st = oracle.population_init(rp, ci, oracle.Params(pop_size=5, seed=2, init_mode=1))
     assert np.array_equal(st.labels, np.tile([1, 0, 2], (5, 1)))
     assert np.all(st.k1 == 1) and np.all(st.k2 == 2)  # intra 0; D = 1, 1
+
+
+# ---------------------------------------------------------------------------
+# The random-stream operators that every run uses (crossover_child,
+# mutate_child and the skip-branch parent of orc_make_offspring_range),
+# re-derived here by brute force: Counter majorities in plain Python, the
+# tournament from the rank/crowding order (pinned in test_oracle_nsga.py),
+# every random word recomputed from Philox (pinned by the published test
+# vectors) with the stream layout written out below, independently of the
+# oracle's own helpers.
+# ---------------------------------------------------------------------------
+
+ST_SELECT, ST_XTIE, ST_MCOIN, ST_MTIE = 2, 3, 4, 5
+
+
+def _node_word(oracle, key, stage, gen, i, v):
+    """Word of (individual i, node v): counter (v, i // 4, gen, stage), word i % 4."""
+    return int(oracle.philox((v, i // 4, gen, stage), key)[i % 4])
+
+
+def _select_word(oracle, key, gen, i, w):
+    """Selection word w of child i: counter (w // 4, i, gen, 2), word w % 4."""
+    return int(oracle.philox((w // 4, i, gen, ST_SELECT), key)[w % 4])
+
+
+def _pick(u, k):
+    return (u * k) >> 32
+
+
+def _majority(values, u):
+    """Most frequent value; among the t tied ones (ascending) the pick(u, t)-th."""
+    cnt = Counter(values)
+    top = max(cnt.values())
+    ties = sorted(c for c, k in cnt.items() if k == top)
+    return ties[_pick(u, len(ties))] if len(ties) > 1 else ties[0]
+
+
+def _brute_offspring(oracle, rp, ci, params, gen, P, k1, k2):
+    """Q of generation `gen` (Alg. 1 parallel map: tournament, Alg. 2
+    crossover, Sec. 4.3.2 mutation) written out node by node."""
+    Np, E, n = params.pop_size, params.n_parents, rp.size - 1
+    key = (params.seed & 0xFFFFFFFF, params.seed >> 32)
+    thr_c = int(np.floor(params.p_crossover * 2.0 ** 32))
+    thr_m = int(np.floor(params.p_mutation * 2.0 ** 32))
+    _, _, order = oracle.rank_crowd_order(k1, k2)
+    Q = np.zeros((Np, n), np.int32)
+    parents, crossed, skipped = [], [], []
+    for i in range(Np):
+        par = []
+        for j in range(E):
+            a = _pick(_select_word(oracle, key, gen, i, 2 * j), Np)
+            b = _pick(_select_word(oracle, key, gen, i, 2 * j + 1), Np)
+            par.append(int(order[min(a, b)]))  # binary tournament on the sorted P
+        cross = _select_word(oracle, key, gen, i, 2 * E) <= thr_c
+        skip = _pick(_select_word(oracle, key, gen, i, 2 * E + 1), E)
+        parents.append(par)
+        crossed.append(cross)
+        skipped.append(skip)
+        if cross:
+            child = [
+                _majority([int(P[p, v]) for p in par], _node_word(oracle, key, ST_XTIE, gen, i, v))
+                for v in range(n)]
+        else:
+            child = [int(x) for x in P[par[skip]]]
+        for v in range(n):
+            nb = ci[rp[v]:rp[v + 1]]
+            Q[i, v] = child[v]
+            if nb.size and _node_word(oracle, key, ST_MCOIN, gen, i, v) < thr_m:
+                Q[i, v] = _majority([child[u] for u in nb], _node_word(oracle, key, ST_MTIE, gen, i, v))
+    return Q, np.array(parents), np.array(crossed), np.array(skipped)
+
+
+def _operator_graph():
+    """Two dense communities, a hub of degree 30, a path, isolated nodes."""
+    rng = np.random.default_rng(5)
+    n = 96
+    u, v = [], []
+    for base in (0, 30):
+        a = rng.integers(base, base + 30, 160)
+        b = rng.integers(base, base + 30, 160)
+        u += list(a)
+        v += list(b)
+    u += [60] * 30
+    v += list(range(61, 91))
+    u += [91, 92]
+    v += [92, 93]  # path 91 - 92 - 93; nodes 94, 95 isolated
+    return synth.csr_from_edges(n, u, v)
+
+
+@pytest.mark.parametrize("cp,mp,seed,alphabet", [
+    (1.0, 0.0, 0, 3),            # crossover only: every node is a vote of E_S parents
+    (0.0, 1.0, 7, 3),            # copy branch, then mutation of every node
+    (0.8, 0.2, (1 << 40) + 3, 4),  # the paper's rates, both key words non-zero
+    (0.8, 0.5, 11, 2),           # two labels: ties at every even degree
+])
+def test_offspring_brute_force(oracle, cp, mp, seed, alphabet):
+    """Every child of two consecutive generations equals the brute-force
+    tournament -> majority crossover (or copy of the skip-branch parent) ->
+    neighbour-majority mutation, with the labels drawn from a small alphabet
+    so that ties (and hence the tie words) decide many nodes."""
+    rp, ci = _operator_graph()
+    n = rp.size - 1
+    m = int(rp[-1] // 2)
+    params = oracle.Params(pop_size=12, n_parents=4, p_crossover=cp, p_mutation=mp, seed=seed)
+    rng = np.random.default_rng(seed & 0xFFFF)
+    ids = rng.choice(n, alphabet, replace=False)
+    P = ids[rng.integers(0, alphabet, (params.pop_size, n))].astype(np.int32)
+    intra, S = oracle.objectives(rp, ci, P)
+    st = oracle.State(P, m - intra, S, 0)
+    for gen in (1, 2):
+        Q, qk1, qk2 = oracle.make_offspring(rp, ci, params, gen, st)
+        want, par, crossed, skip = _brute_offspring(oracle, rp, ci, params, gen, st.labels, st.k1, st.k2)
+        opar, oxo, oskip = oracle.select_parents(params, gen, st.k1, st.k2)
+        assert np.array_equal(opar, par), "tournament parents differ"
+        assert np.array_equal(oxo.astype(bool), crossed), "crossover coins differ"
+        assert np.array_equal(oskip, skip), "skip-branch parent differs"
+        assert np.array_equal(Q, want), "offspring differ from the brute-force operators"
+        i2, s2 = oracle.objectives(rp, ci, Q)
+        assert np.array_equal(qk1, m - i2) and np.array_equal(qk2, s2)
+        if cp == 1.0:
+            assert crossed.all()
+        if cp == 0.0:
+            assert not crossed.any()
+        st = oracle.run(rp, ci, params, st, 1)
+
+
+def test_mutation_takes_the_majority_not_any_neighbour(oracle):
+    """A node whose neighbours hold labels {a, a, a, b} must take a under
+    mutation at rate 1 (a random neighbour label would give b a quarter of
+    the time): the hub 0 with neighbours 1..4, all copies of one parent."""
+    rp, ci = synth.csr_from_edges(5, [0, 0, 0, 0], [1, 2, 3, 4])
+    params = oracle.Params(pop_size=40, n_parents=2, p_crossover=0.0, p_mutation=1.0, seed=3)
+    P = np.tile(np.array([4, 2, 2, 2, 3], np.int32), (params.pop_size, 1))
+    intra, S = oracle.objectives(rp, ci, P)
+    st = oracle.State(P, 4 - intra, S, 0)
+    Q, _, _ = oracle.make_offspring(rp, ci, params, 1, st)
+    assert np.all(Q[:, 0] == 2)        # neighbours 2, 2, 2, 3
+    assert np.all(Q[:, 1:] == 4)       # each leaf sees only the hub's label 4

@@ -71,3 +71,24 @@ def test_reproducible_and_resumable(oracle):
     assert np.array_equal(a.labels, b.labels) and np.array_equal(a.k1, b.k1)
     c = oracle.run(rp, ci, oracle.Params(pop_size=24, seed=78), st0, 6)
     assert not np.array_equal(a.labels, c.labels)
+
+
+def test_threaded_helpers_match_the_sequential_oracle(oracle):
+    """The test-side helpers that split a generation's children (or a set of
+    labellings) over host threads give exactly what the sequential oracle
+    gives: same offspring, same keys, same next population."""
+    import synth
+    rp, ci = synth.lfr_style(2000, 12, 30, 0.3, seed=3)[:2]
+    params = oracle.Params(pop_size=30, seed=77)
+    st = oracle.population_init(rp, ci, params)
+    seq = oracle.run(rp, ci, params, st, 3)
+    par = oracle.run_parallel(rp, ci, params, st, 3, threads=5)
+    assert par.generation == seq.generation == 3
+    assert np.array_equal(par.labels, seq.labels)
+    assert np.array_equal(par.k1, seq.k1) and np.array_equal(par.k2, seq.k2)
+    Q, a, b = oracle.make_offspring(rp, ci, params, 4, seq)
+    Q2, a2, b2 = oracle.make_offspring_parallel(rp, ci, params, 4, seq, threads=7)
+    assert np.array_equal(Q, Q2) and np.array_equal(a, a2) and np.array_equal(b, b2)
+    i1, s1 = oracle.objectives(rp, ci, Q)
+    i2, s2 = oracle.objectives_parallel(rp, ci, Q, threads=3)
+    assert np.array_equal(i1, i2) and np.array_equal(s1, s2)
