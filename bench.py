@@ -62,6 +62,10 @@ def parse_args(argv=None):
     ap.add_argument("--policy", type=int, default=0, help="server admission: 0 FIFO, 1 shortest work first")
     ap.add_argument("--preroll-s", type=float, default=0.5,
                     help="seconds of extra untimed generations before timing (clock settling)")
+    ap.add_argument("--large", default="lfr-1m",
+                    help="workload of the HBM-bound leg (a whole G-generation run with per-stage events); "
+                         "'none' skips it")
+    ap.add_argument("--large-generations", type=int, default=100)
     return ap.parse_args(argv)
 
 
@@ -110,9 +114,25 @@ def build_workload(args):
     return rp, ci, desc
 
 
-def algorithmic_bytes(n: int, m: int, np_: int, p_mut: float) -> dict:
-    """Bytes each kernel must move with no reuse beyond what it stages
-    explicitly (node-major rows of W int32; CSR int32)."""
+def algorithmic_bytes(n: int, m: int, np_: int, p_mut: float, es: int = 4) -> dict:
+    """Per-launch bytes of each kernel under the per-individual model of the
+    method (every individual's label vector read and written as its own
+    array, the CSR and the neighbour labels gathered per individual; int32
+    labels and CSR): evaluation 16m + 8n, crossover 4 E_S n + 4n, mutation
+    4n + 4n + M_P (16m + 8n) bytes per individual, times N_p."""
+    return {
+        "crossover": np_ * (4 * es * n + 4 * n),
+        "mutation": np_ * (8 * n + p_mut * (16 * m + 8 * n)),
+        "evaluate": np_ * (16 * m + 8 * n),
+        "select": 0,
+    }
+
+
+def access_bytes(n: int, m: int, np_: int, p_mut: float) -> dict:
+    """Per-launch bytes of the node-major kernels as built (rows of W int32
+    labels per node, the CSR streamed once per population, each undirected
+    edge read from its lower end), with no reuse beyond what a kernel stages
+    explicitly."""
     W = (np_ + 3) & ~3
     csr = 4 * (n + 1) + 4 * 2 * m
     return {
@@ -124,6 +144,24 @@ def algorithmic_bytes(n: int, m: int, np_: int, p_mut: float) -> dict:
         "evaluate": 4 * W * n + 4 * W * m + 8 * np_ * n + csr,
         "select": 0,
     }
+
+
+def kernel_roofline(kernel: str, ms: float, n: int, m: int, np_: int, p_mut: float, peak: float,
+                    peak_kind: str, workload: str) -> dict:
+    """HBM roofline of one kernel from its mean CUDA-event duration: the
+    per-individual bytes of the method (``achieved``/``frac``) and the
+    node-major access bytes (``*_access``) side by side, and the ncu DRAM
+    traffic per launch when a committed summary was taken on this source."""
+    alg = algorithmic_bytes(n, m, np_, p_mut)[kernel]
+    acc = access_bytes(n, m, np_, p_mut)[kernel]
+    a = alg / (ms / 1e3) / 1e9
+    b = acc / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": kernel, "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak,
+            "peak_source": peak_kind, "traffic": recorded_traffic(kernel, workload),
+            "bytes_model": "per-individual (16m + 8n evaluation; 4 E_S n + 4n crossover; "
+                           "8n + M_P (16m + 8n) mutation; x N_p)",
+            "algorithmic_bytes_per_launch": alg, "launch_ms": ms,
+            "access_bytes_per_launch": acc, "achieved_access": b, "frac_access": b / peak}
 
 
 def measured_peaks():
@@ -162,6 +200,11 @@ def recorded_traffic(kernel: str, workload: str):
 # ---------------------------------------------------------------------------
 # Clock sampling during the timed region
 # ---------------------------------------------------------------------------
+
+def _gpu_index() -> int:
+    """nvidia-smi index of this process's (first visible) GPU."""
+    return int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or 0)
+
 
 class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
@@ -221,6 +264,28 @@ class ClockSampler:
 # CPU oracle legs
 # ---------------------------------------------------------------------------
 
+def cpu_description() -> dict:
+    """The host CPU the oracle runs on: model name (lscpu, else /proc/cpuinfo,
+    else the platform string) and the number of online cores."""
+    import platform
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model and os.path.exists("/proc/cpuinfo"):
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    return {"cpu_model": model or platform.processor() or platform.machine(), "nproc": os.cpu_count()}
+
+
 def cpu_oracle_sample(rp, ci, seed: int, budget_s: float = 12.0, max_gens: int = 6):
     """The oracle as it stands, single-threaded, for whole generations of the
     same workload until the budget is spent."""
@@ -238,7 +303,7 @@ def cpu_oracle_sample(rp, ci, seed: int, budget_s: float = 12.0, max_gens: int =
     dt = time.perf_counter() - t0
     return {"value": params.pop_size * m * gens / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{gens} whole generations (N_p={params.pop_size}) of the same workload, "
-                      f"single-threaded C oracle, {dt:.1f} s"}
+                      f"single-threaded C oracle, {dt:.1f} s", **cpu_description()}
 
 
 def run_reference(args):
@@ -274,7 +339,8 @@ def run_reference(args):
                    "step": f"{chunk} of the {params.pop_size} children of one generation "
                            "(crossover, mutation, evaluation) by the CPU oracle"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} steps x {chunk} children, single-threaded C oracle"},
+                         "sample": f"{args.steps} steps x {chunk} children, single-threaded C oracle",
+                         **cpu_description()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -284,6 +350,63 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+
+def large_leg(args, dev, stream, peak, peak_kind):
+    """HBM-bound leg: a whole run of the large workload (generations
+    1..G of a fresh population, per-stage CUDA events on every generation,
+    L2 flushed between generations), where the label matrix and the degree
+    histogram no longer fit in L2. Reports the mean stage times and the HBM
+    roofline of the evaluation and mutation kernels over the run."""
+    import torch
+    import paper_2506_01752_gb300 as mocd
+    import synth
+
+    spec = synth.WORKLOADS[args.large]
+    rp, ci, _ = synth.workload(args.large, seed=0)
+    n, m = int(rp.size - 1), int(rp[-1] // 2)
+    params = mocd.Params(seed=args.seed)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ctx = mocd.graph_upload(rp, ci, stream)
+    try:
+        mocd.population_init(ctx, params)
+        mocd.set_timing(ctx, True)
+        mocd.generation(ctx, 3)  # warm-up, then a fresh run
+        mocd.population_init(ctx, params)
+        mocd.synchronize(ctx)
+        sampler = ClockSampler(_gpu_index())
+        sampler.start()
+        step_ms, stages = [], {s: [] for s in mocd.STAGES}
+        for _ in range(args.large_generations):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev0.record(stream)
+            mocd.generation(ctx, 1)
+            ev1.record(stream)
+            ev1.synchronize()
+            step_ms.append(ev0.elapsed_time(ev1))
+            for s_, v in mocd.kernel_times(ctx).items():
+                stages[s_].append(v)
+        clocks = sampler.stop()
+    finally:
+        mocd.destroy(ctx)
+    mean = {s_: statistics.fmean(v) for s_, v in stages.items()}
+    G = args.large_generations
+    return {
+        "workload": f"{args.large}: LFR-style n={n}, m={m}, avg deg {spec['avg_deg']}, max {spec['max_deg']}, "
+                    f"communities {spec['cmin']}-{spec['cmax']}, mu={spec['mu']}",
+        "generations": f"1-{G} of a fresh run, per-stage events on every generation, L2 flushed between",
+        "value": params.pop_size * m * G / (sum(step_ms) / 1e3), "unit": UNIT,
+        "ms_per_step": sum(step_ms) / G,
+        "stage_ms": {k: round(v, 4) for k, v in mean.items()},
+        "evaluate": kernel_roofline("evaluate", mean["evaluate"], n, m, params.pop_size, params.p_mutation,
+                                    peak, peak_kind, args.large),
+        "mutation": kernel_roofline("mutation", mean["mutation"], n, m, params.pop_size, params.p_mutation,
+                                    peak, peak_kind, args.large),
+        "clocks": clocks,
+    }
+
 
 def run_mine(args):
     import torch
@@ -364,21 +487,14 @@ def run_mine(args):
     mean_stage = {s: statistics.fmean(v) for s, v in stages.items()}
     kernels = {k: mean_stage[k] for k in ("crossover", "mutation", "evaluate", "select")}
     dominant = max(kernels, key=kernels.get)
-    alg = algorithmic_bytes(n, m, params.pop_size, params.p_mutation)
     peak, peak_kind = measured_peaks()
-    achieved = alg[dominant] / (kernels[dominant] / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind,
-                "traffic": recorded_traffic(dominant, args.workload),
-                "algorithmic_bytes_per_launch": alg[dominant],
-                "stage_ms": {k: round(v, 5) for k, v in mean_stage.items()},
-                "stage_events_every": every}
+    roofline = kernel_roofline(dominant, kernels[dominant], n, m, params.pop_size, params.p_mutation, peak,
+                               peak_kind, args.workload)
+    roofline["stage_ms"] = {k: round(v, 5) for k, v in mean_stage.items()}
+    roofline["stage_events_every"] = every
     # The objective (evaluation) kernel, against the same HBM roofline.
-    ev_achieved = alg["evaluate"] / (kernels["evaluate"] / 1e3) / 1e9
-    roofline_objective = {"bound": "hbm", "kernel": "evaluate", "achieved": ev_achieved, "peak": peak,
-                          "unit": "GB/s", "frac": ev_achieved / peak, "peak_source": peak_kind,
-                          "traffic": recorded_traffic("evaluate", args.workload),
-                          "algorithmic_bytes_per_launch": alg["evaluate"]}
+    roofline_objective = kernel_roofline("evaluate", kernels["evaluate"], n, m, params.pop_size,
+                                         params.p_mutation, peak, peak_kind, args.workload)
 
     e2e = None
     if not args.no_e2e:
@@ -402,6 +518,9 @@ def run_mine(args):
                "job_ms": round(e2e_t, 3)}
 
     mocd.destroy(ctx)
+    large = None
+    if world == 1 and args.large != "none":
+        large = large_leg(args, dev, stream, peak, peak_kind)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(rp, ci, args.seed)
@@ -420,6 +539,7 @@ def run_mine(args):
                        "timed_generations": f"1-{args.steps} of a fresh run (population re-initialised after the warm-up)"},
             "roofline": roofline,
             "roofline_objective": roofline_objective,
+            "roofline_hbm": large,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": 4 * args.steps,
@@ -479,6 +599,8 @@ def run_batch(args):
 
     mocd.batch_generation(b, args.warmup)
     mocd.batch_synchronize(b)
+    sampler = ClockSampler(_gpu_index())
+    sampler.start()
     batch_ms = timed(lambda: mocd.batch_generation(b, 1))
     mocd.batch_synchronize(b)
     mocd.batch_destroy(b)
@@ -506,6 +628,7 @@ def run_batch(args):
             mocd.synchronize(c)
             per_job[k] += (time.perf_counter() - t0) * 1e3
         plain_ms.append((time.perf_counter() - t0) * 1e3)
+    clocks = sampler.stop()
     for c in ctxs:
         mocd.destroy(c)
 
@@ -530,7 +653,7 @@ def run_batch(args):
                    "autotuned_nodes_per_warp": shape,
                    "plain": "per-instance generation graph, instances one after another",
                    "l2": f"flushed between timed steps ({FLUSH_BYTES >> 20} MB write)"},
-        "n_gpus": 1, "higher_is_better": True, "dtype": "int32", "data": "synthetic",
+        "n_gpus": 1, "higher_is_better": True, "dtype": "int32", "data": "synthetic", "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -568,6 +691,8 @@ def run_serve(args):
     mocd.pareto_front(h)
     mocd.destroy(h)
 
+    sampler = ClockSampler(_gpu_index())
+    sampler.start()
     # Continuous-batching server (background scheduler + admission workers).
     srv = mocd.Server(args.hbm_budget_gb << 30, max_running=args.max_running, depth=args.depth)
     srv.start(admission_threads=2, policy=args.policy)
@@ -605,6 +730,7 @@ def run_serve(args):
         mocd.destroy(h)
         plain_lat.append(time.perf_counter() - t0 - arrivals[i])
     plain_make = time.perf_counter() - t0
+    clocks = sampler.stop()
 
     line = {
         "metric": "detection request latency p50/p99 (s) and edge-evals/s [serving]",
@@ -616,7 +742,7 @@ def run_serve(args):
                    "admission": "shortest work first" if args.policy else "first come first served",
                    "admission_threads": 2,
                    "pool": [d for _, _, d in pool]},
-        "n_gpus": 1, "dtype": "int32", "data": "synthetic",
+        "n_gpus": 1, "dtype": "int32", "data": "synthetic", "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -639,6 +765,8 @@ def run_quality(args):
     stream = torch.cuda.Stream()
     G = 100
     rows = []
+    sampler = ClockSampler(_gpu_index())
+    sampler.start()
     for mu in (0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7):
         rp, ci, truth = synth.workload("lfr-40k", seed=args.seed, mu=mu)
         m = int(rp[-1] // 2)
@@ -667,8 +795,9 @@ def run_quality(args):
                 "nmi": round(quality.nmi(lab, truth), 4), "ami": round(quality.ami(lab, truth), 4),
                 "f1": round(quality.pairwise_f1(lab, truth), 4),
             })
+    clocks = sampler.stop()
     line = {
-        "metric": "whole-run quality and run time (G = 100)", "unit": "NMI / ms",
+        "metric": "whole-run quality and run time (G = 100)", "unit": "NMI / ms", "clocks": clocks,
         "workload": "lfr-40k mixing sweep", "rows": rows, "n_gpus": 1, "dtype": "int32",
         "data": "synthetic", "config": {"workload": "lfr-40k", "N_p": 100, "G": G, "E_S": 4,
                                         "C_P": 0.8, "M_P": 0.2, "seed": args.seed},

@@ -230,8 +230,10 @@ int mocd_evaluate(mocd_ctx *ctx, int32_t count, const int32_t *labels, int64_t *
  *   cuda_stream   stream to issue on (NULL: the legacy default stream)
  * The call is asynchronous on the stream and calls no cudaMalloc/cudaFree.
  * The first call on each device looks up the scratch's device address
- * (cudaGetSymbolAddress) on the current device; make that first call before
- * any stream capture. All calls share the one scratch array, which keeps the
+ * (cudaGetSymbolAddress) on the current device and keeps it for the rest of
+ * the process; make that first call before any stream capture, and do not
+ * call the entry point again after a cudaDeviceReset of that device (the kept
+ * address would be stale). All calls share the one scratch array, which keeps the
  * previous call's contents (the call clears what it needs), so calls that
  * overlap on the GPU -- e.g. on two streams at once -- race and give wrong
  * results; serialise them.
@@ -306,6 +308,13 @@ void mocd_batch_destroy(mocd_batch *b);
  *                       policy 1 admits the queued job with the least work
  *                       ((n + 2m) x (G + 1)) first.
  * Calls on one server may come from any host thread.
+ *   mocd_job_footprint  the device bytes the server accounts for a job while
+ *                       it runs (admission compares their sum with the budget):
+ *                       the four label buffers and the degree histogram
+ *                       (5 x 4 n W bytes, W = N_p rounded up to a multiple of
+ *                       4), the CSR and node order, the individual-major
+ *                       buffer of the front download (4 n N_p) and 1 MiB of
+ *                       small state. Errors: INVALID_ARG.
  */
 typedef struct mocd_server mocd_server;
 int mocd_server_create(mocd_server **out, int64_t hbm_budget_bytes, int32_t max_running, int32_t depth);
@@ -317,6 +326,33 @@ int mocd_server_job_state(mocd_server *s, int64_t job_id, int32_t *state, int32_
 int mocd_server_result(mocd_server *s, int64_t job_id, int32_t cap, int32_t *count, int32_t *labels,
                        double *f1, double *f2, int64_t *intra, int64_t *sumsq, int32_t *best);
 void mocd_server_destroy(mocd_server *s);
+int mocd_job_footprint(int64_t n, int64_t nnz, int32_t pop_size, int64_t *bytes);
+
+/*
+ * Test support (not a step of the method): host-side failure injection, so
+ * that error paths can be exercised without any GPU fault. After `skip`
+ * further calls at `site` succeed, the next `count` calls there fail; the
+ * setting is process-wide and count = 0 disarms the site.
+ *   MOCD_SITE_DEVICE_ALLOC  every device allocation of the library fails as
+ *                           if the device were out of memory (the calling
+ *                           entry point returns OUT_OF_MEMORY; `status` is
+ *                           ignored)
+ *   MOCD_SITE_GENERATION    mocd_generation returns `status` (a negative
+ *                           MOCD_ERR_* code) without launching anything
+ * Errors: INVALID_ARG (unknown site, negative skip or count, non-negative
+ * status for the generation site).
+ */
+enum { MOCD_SITE_DEVICE_ALLOC = 0, MOCD_SITE_GENERATION = 1 };
+int mocd_debug_inject(int32_t site, int32_t skip, int32_t count, int32_t status);
+
+/*
+ * Test support: bytes in use now and the high-water mark since the last
+ * reset in the current device's default stream-ordered memory pool, from
+ * which every device allocation of the library comes (reset_peak != 0 first
+ * resets the mark to the current use). Either pointer may be NULL.
+ * Errors: CUDA.
+ */
+int mocd_debug_pool_usage(int32_t reset_peak, int64_t *current, int64_t *peak);
 
 /* Block until all work issued on the context stream is done. */
 int mocd_synchronize(mocd_ctx *ctx);

@@ -23,7 +23,8 @@ __all__ = [
     "get_population", "get_offspring", "set_population", "evaluate", "synchronize",
     "set_timing", "kernel_times", "info", "destroy", "status_string", "evaluate_noalloc",
     "batch_create", "batch_generation", "batch_autotune", "batch_synchronize", "batch_destroy",
-    "Server", "FrontStats", "front_stats", "select_solution",
+    "Server", "FrontStats", "front_stats", "select_solution", "job_footprint", "debug_inject",
+    "debug_pool_usage", "SITE_DEVICE_ALLOC", "SITE_GENERATION",
     "SELECT_MODULARITY", "SELECT_COMMUNITIES", "SELECT_SIZE_VARIANCE", "SELECT_MEAN_CONDUCTANCE",
     "SELECT_MAX_CONDUCTANCE", "STAGES",
 ]
@@ -120,6 +121,9 @@ def load():
         "mocd_server_job_state": (ctypes.c_int, [P, i64, P, P]),
         "mocd_server_result": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, P]),
         "mocd_server_destroy": (None, [P]),
+        "mocd_job_footprint": (ctypes.c_int, [i64, i64, i32, P]),
+        "mocd_debug_inject": (ctypes.c_int, [i32, i32, i32, i32]),
+        "mocd_debug_pool_usage": (ctypes.c_int, [i32, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -372,6 +376,32 @@ class Server:
         if self.h is not None and self.h.value:
             load().mocd_server_destroy(self.h)
             self.h.value = None
+
+
+def job_footprint(n: int, nnz: int, pop_size: int = 100) -> int:
+    """Device bytes the server accounts for a job while it runs."""
+    out = ctypes.c_int64()
+    _check(load().mocd_job_footprint(int(n), int(nnz), int(pop_size), ctypes.byref(out)), "mocd_job_footprint")
+    return out.value
+
+
+SITE_DEVICE_ALLOC = 0
+SITE_GENERATION = 1
+
+
+def debug_inject(site: int, skip: int = 0, count: int = 1, status: int = -8):
+    """Host-side failure injection (test support): after `skip` calls at
+    `site` pass, the next `count` fail; count 0 disarms."""
+    _check(load().mocd_debug_inject(int(site), int(skip), int(count), int(status)), "mocd_debug_inject")
+
+
+def debug_pool_usage(reset_peak: bool = False):
+    """(bytes in use, high-water mark) of the device's default memory pool."""
+    cur = ctypes.c_int64()
+    peak = ctypes.c_int64()
+    _check(load().mocd_debug_pool_usage(1 if reset_peak else 0, ctypes.byref(cur), ctypes.byref(peak)),
+           "mocd_debug_pool_usage")
+    return cur.value, peak.value
 
 
 def synchronize(ctx):

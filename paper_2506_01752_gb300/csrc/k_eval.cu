@@ -128,10 +128,13 @@ evaluate_kernel(int n, int W, int count, const int32_t *__restrict__ row_ptr,
 
 }  // namespace
 
-int grid_for_eval(int sms)
+int grid_for_eval(int sms, bool label_major)
 {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, evaluate_kernel<true>, kBlock, 0);
+    if (label_major)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, evaluate_kernel<true>, kBlock, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, evaluate_kernel<false>, kBlock, 0);
     if (per_sm < 1) per_sm = 1;
     return sms * per_sm;
 }

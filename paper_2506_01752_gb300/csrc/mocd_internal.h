@@ -23,6 +23,16 @@ namespace mocd {
 // Record `ev` on the context's stream (after all work issued so far).
 int record_on_stream(mocd_ctx *c, cudaEvent_t ev);
 
+// Every device allocation of the library (stream-ordered cudaMallocAsync);
+// fails with cudaErrorMemoryAllocation when a test injects a failure there.
+cudaError_t dev_alloc(void **p, size_t bytes, cudaStream_t st);
+
+// Host-side failure injection (mocd_debug_inject): true if the next call at
+// `site` is to fail; *status (if given) receives the status to return.
+constexpr int kSiteDeviceAlloc = 0;
+constexpr int kSiteGeneration = 1;
+bool inject_failure(int site, int *status);
+
 constexpr int kMaxPop = 128;      // N_p limit: one int4 of labels per lane per row
 constexpr int kMaxParents = 16;   // E_S limit
 constexpr int kBlock = 256;       // threads per block of the node-parallel kernels
@@ -106,7 +116,8 @@ cudaError_t launch_to_node_major(int n, int W, int count, const int32_t *src, in
 cudaError_t launch_symmetry_check(int n, const int32_t *row_ptr, const int32_t *col_idx, int *bad, int sms,
                                   cudaStream_t s);
 // Occupancy-derived grid sizes.
-int grid_for_eval(int sms);
+// Resident blocks of the evaluation kernel in the given histogram layout.
+int grid_for_eval(int sms, bool label_major = true);
 int grid_for_crossover(int sms, int es);
 int grid_for_mutation(int sms, int hash_size, int *smem_bytes);
 int mutation_warps_per_block();

@@ -15,7 +15,9 @@
 // holds it (16 MiB + 2 KiB) until the process exits. On the host its name is
 // only a stand-in, never a device address, so the address is fetched once per
 // device with cudaGetSymbolAddress (the first call on each device does that)
-// and then passed to the kernels.
+// and then passed to the kernels. The cached address belongs to the device's
+// primary context of that moment: after a cudaDeviceReset the entry point
+// must not be used again in the same process.
 #include <mutex>
 
 #include "mocd.h"
@@ -86,9 +88,9 @@ extern "C" int mocd_evaluate_noalloc(const int32_t *row_ptr, const int32_t *col_
     if (cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * (kAccWords + (size_t)count * (size_t)n), s) != cudaSuccess)
         return MOCD_ERR_CUDA;
     int sms = 1;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (launch_evaluate((int)n, W, count, row_ptr, col_idx, labels, hist, acc, grid_for_eval(sms), s, nullptr,
-                        false) != cudaSuccess)
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MOCD_ERR_CUDA;
+    if (launch_evaluate((int)n, W, count, row_ptr, col_idx, labels, hist, acc, grid_for_eval(sms, false), s,
+                        nullptr, false) != cudaSuccess)
         return MOCD_ERR_CUDA;
     finish_keys_kernel<<<1, kMaxPop, 0, s>>>(count, acc, intra, sumsq);
     if (cudaGetLastError() != cudaSuccess) return MOCD_ERR_CUDA;

@@ -117,7 +117,7 @@ int grow(cudaStream_t st, T **p, size_t *cap, size_t need)
     *p = nullptr;
     *cap = 0;
     void *q = nullptr;
-    cudaError_t e = cudaMallocAsync(&q, std::max<size_t>(need, 1) * sizeof(T), st);
+    cudaError_t e = dev_alloc(&q, std::max<size_t>(need, 1) * sizeof(T), st);
     if (e != cudaSuccess) return cuda_status(e);
     *p = static_cast<T *>(q);
     *cap = need;
@@ -197,7 +197,7 @@ int prepare_population(mocd_ctx *c, const mocd_params *p)
         int32_t *b[4] = {};
         for (int k = 0; k < 4; ++k) {
             void *q = nullptr;
-            cudaError_t e = cudaMallocAsync(&q, cells * sizeof(int32_t), c->stream);
+            cudaError_t e = dev_alloc(&q, cells * sizeof(int32_t), c->stream);
             if (e != cudaSuccess) {
                 for (int j = 0; j < k; ++j) dev_free(b[j], c->stream);
                 return cuda_status(e);
@@ -208,7 +208,6 @@ int prepare_population(mocd_ctx *c, const mocd_params *p)
         c->ps.buf[1] = b[1];
         c->ps.q = b[2];
         c->ps.c = b[3];
-        c->pop_cells = cells;
         // Small per-generation state in one allocation.
         const size_t bytes = sizeof(unsigned long long) * 2 * kMaxPop   // acc
                              + sizeof(int64_t) * 2 * kMaxPop              // pk
@@ -222,9 +221,13 @@ int prepare_population(mocd_ctx *c, const mocd_params *p)
                              + sizeof(double) * 2 * kMaxPop               // fval
                              + 64;                                        // gen, alignment
         void *s = nullptr;
-        cudaError_t e = cudaMallocAsync(&s, bytes, c->stream);
-        if (e != cudaSuccess) return cuda_status(e);
+        cudaError_t e = dev_alloc(&s, bytes, c->stream);
+        if (e != cudaSuccess) {
+            free_population(c);  // the label buffers too: pop_cells stays 0
+            return cuda_status(e);
+        }
         c->d_small = s;
+        c->pop_cells = cells;  // every population buffer exists from here on
         char *q = static_cast<char *>(s);
         c->ps.acc = reinterpret_cast<unsigned long long *>(q); q += sizeof(unsigned long long) * 2 * kMaxPop;
         c->ps.pk = reinterpret_cast<int64_t *>(q); q += sizeof(int64_t) * 2 * kMaxPop;
@@ -426,7 +429,7 @@ int download_r(mocd_ctx *c, const int32_t *ridx, int count, int32_t *labels)
     if (rc) return rc;
     if (!c->d_idx) {
         void *q = nullptr;
-        CK(cudaMallocAsync(&q, sizeof(int32_t) * 2 * kMaxPop, c->stream));
+        CK(dev_alloc(&q, sizeof(int32_t) * 2 * kMaxPop, c->stream));
         c->d_idx = static_cast<int32_t *>(q);
     }
     CK(cudaMemcpyAsync(c->d_idx, ridx, sizeof(int32_t) * count, cudaMemcpyHostToDevice, c->stream));
@@ -482,7 +485,7 @@ int front_stats(mocd_ctx *c, int count, std::vector<unsigned long long> &out)
     const size_t acc_words = stats_acc_words();
     if (!c->d_stats) {
         void *p = nullptr;
-        CK(cudaMallocAsync(&p, sizeof(unsigned long long) * (acc_words + 4 * kMaxPop), c->stream));
+        CK(dev_alloc(&p, sizeof(unsigned long long) * (acc_words + 4 * kMaxPop), c->stream));
         c->d_stats = static_cast<unsigned long long *>(p);
     }
     CK(cudaMemsetAsync(c->d_volsize, 0, sizeof(unsigned long long) * n * (size_t)count, c->stream));
@@ -564,6 +567,43 @@ int select_member(const std::vector<FrontMember> &mem, int criterion, int64_t ta
 }
 
 }  // namespace
+
+namespace {
+
+// Host-side failure injection (mocd_debug_inject): per site, the number of
+// calls still to pass, then the number to fail and the status to fail with.
+struct InjectSite {
+    int skip = 0, count = 0, status = 0;
+};
+std::mutex g_inject_mu;
+InjectSite g_inject[2];
+std::atomic<bool> g_inject_armed{false};  // some site has failures pending
+
+}  // namespace
+
+bool mocd::inject_failure(int site, int *status)
+{
+    if (!g_inject_armed.load(std::memory_order_relaxed)) return false;
+    std::lock_guard<std::mutex> lock(g_inject_mu);
+    InjectSite &q = g_inject[site];
+    if (q.count <= 0) return false;
+    if (q.skip > 0) {
+        --q.skip;
+        return false;
+    }
+    --q.count;
+    if (status) *status = q.status;
+    return true;
+}
+
+cudaError_t mocd::dev_alloc(void **p, size_t bytes, cudaStream_t st)
+{
+    if (inject_failure(kSiteDeviceAlloc, nullptr)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync(p, bytes, st);
+}
 
 int mocd::record_on_stream(mocd_ctx *c, cudaEvent_t ev)
 {
@@ -673,10 +713,10 @@ int mocd_graph_upload(mocd_ctx **out, int64_t n, const int64_t *row_ptr, const i
     std::vector<int32_t> rp32(n + 1);
     for (int64_t v = 0; v <= n; ++v) rp32[v] = (int32_t)row_ptr[v];
     void *p = nullptr;
-    cudaError_t e = cudaMallocAsync(&p, sizeof(int32_t) * (n + 1), c->stream);
+    cudaError_t e = dev_alloc(&p, sizeof(int32_t) * (n + 1), c->stream);
     if (e != cudaSuccess) return fail(cuda_status(e));
     c->d_row_ptr = static_cast<int32_t *>(p);
-    e = cudaMallocAsync(&p, sizeof(int32_t) * nnz, c->stream);
+    e = dev_alloc(&p, sizeof(int32_t) * nnz, c->stream);
     if (e != cudaSuccess) return fail(cuda_status(e));
     c->d_col_idx = static_cast<int32_t *>(p);
     // Work order of the degree-proportional kernels: degree descending (ties
@@ -689,7 +729,7 @@ int mocd_graph_upload(mocd_ctx **out, int64_t n, const int64_t *row_ptr, const i
         for (size_t d = 1; d < at.size(); ++d) at[d] += at[d - 1];
         for (int64_t v = 0; v < n; ++v) order[at[(size_t)(dmax - (row_ptr[v + 1] - row_ptr[v]))]++] = (int32_t)v;
     }
-    e = cudaMallocAsync(&p, sizeof(int32_t) * n, c->stream);
+    e = dev_alloc(&p, sizeof(int32_t) * n, c->stream);
     if (e != cudaSuccess) return fail(cuda_status(e));
     c->d_order = static_cast<int32_t *>(p);
     if (cudaMemcpyAsync(c->d_order, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream) !=
@@ -697,7 +737,7 @@ int mocd_graph_upload(mocd_ctx **out, int64_t n, const int64_t *row_ptr, const i
         return fail(MOCD_ERR_CUDA);
     int *d_bad = nullptr;
     int h_bad = 0;
-    e = cudaMallocAsync(reinterpret_cast<void **>(&d_bad), sizeof(int), c->stream);
+    e = dev_alloc(reinterpret_cast<void **>(&d_bad), sizeof(int), c->stream);
     if (e != cudaSuccess) return fail(cuda_status(e));
     const bool copied =
         cudaMemcpyAsync(c->d_row_ptr, rp32.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice,
@@ -720,6 +760,8 @@ int mocd_population_init(mocd_ctx *c, const mocd_params *params)
     int rc = check_params(c, params);
     if (rc) return rc;
     CK(cudaSetDevice(c->device));
+    // Until the new population is complete, nothing may run on the old one.
+    c->ready = false;
     rc = prepare_population(c, params);
     if (rc) return rc;
     CK(launch_init_population(c->gp, params->init_mode, c->d_row_ptr, c->d_col_idx, c->ps.buf[1], c->stream));
@@ -734,6 +776,7 @@ int mocd_set_population(mocd_ctx *c, const mocd_params *params, const int32_t *l
     rc = validate_labels(c, labels, (size_t)params->pop_size * (size_t)c->n);
     if (rc) return rc;
     CK(cudaSetDevice(c->device));
+    c->ready = false;
     rc = prepare_population(c, params);
     if (rc) return rc;
     rc = grow(c->stream, &c->d_im, &c->im_cap, (size_t)params->pop_size * (size_t)c->n);
@@ -749,6 +792,8 @@ int mocd_generation(mocd_ctx *c, int32_t n_generations)
 {
     if (!c || n_generations < 0) return MOCD_ERR_INVALID_ARG;
     if (!c->ready) return MOCD_ERR_NOT_READY;
+    int injected = 0;
+    if (n_generations > 0 && inject_failure(kSiteGeneration, &injected)) return injected;
     const int g = c->timing ? 1 : 0;
     if (!c->graph_exec[g]) {
         const int rc = build_graph(c);
@@ -894,7 +939,7 @@ int mocd_evaluate(mocd_ctx *c, int32_t count, const int32_t *labels, int64_t *in
     if ((rc = grow(c->stream, &c->d_eval_hist, &c->eval_hist_cap, (size_t)((batch + 3) & ~3) * n))) return rc;
     if (!c->d_eval_acc) {
         void *q = nullptr;
-        CK(cudaMallocAsync(&q, sizeof(unsigned long long) * 2 * kMaxPop, c->stream));
+        CK(dev_alloc(&q, sizeof(unsigned long long) * 2 * kMaxPop, c->stream));
         c->d_eval_acc = static_cast<unsigned long long *>(q);
     }
     const int grid = grid_for_eval(c->sms);
@@ -1119,6 +1164,35 @@ void mocd_batch_destroy(mocd_batch *b)
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
+}
+
+int mocd_debug_inject(int32_t site, int32_t skip, int32_t count, int32_t status)
+{
+    if (site != MOCD_SITE_DEVICE_ALLOC && site != MOCD_SITE_GENERATION) return MOCD_ERR_INVALID_ARG;
+    if (skip < 0 || count < 0 || (count > 0 && site == MOCD_SITE_GENERATION && status >= 0))
+        return MOCD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_inject_mu);
+    g_inject[site] = InjectSite{skip, count, status};
+    g_inject_armed.store(g_inject[0].count > 0 || g_inject[1].count > 0, std::memory_order_relaxed);
+    return MOCD_OK;
+}
+
+int mocd_debug_pool_usage(int32_t reset_peak, int64_t *current, int64_t *peak)
+{
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    cudaMemPool_t pool = nullptr;
+    CK(cudaDeviceGetDefaultMemPool(&pool, dev));
+    if (reset_peak) {
+        unsigned long long zero = 0;
+        CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+    }
+    unsigned long long cur = 0, hi = 0;
+    CK(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &cur));
+    CK(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &hi));
+    if (current) *current = (int64_t)cur;
+    if (peak) *peak = (int64_t)hi;
+    return MOCD_OK;
 }
 
 void mocd_destroy(mocd_ctx *c)

@@ -40,6 +40,7 @@ struct Job {
     mocd_params params{};
     int32_t generations = 0;
     int32_t issued = 0;
+    int issue_error = MOCD_OK;  // first failure while issuing generations
     int64_t footprint = 0;
     double work = 0.0;  // relative cost, for shortest-first admission
     mocd_ctx *ctx = nullptr;
@@ -51,12 +52,12 @@ struct Job {
     std::vector<int64_t> intra, sumsq;
 };
 
-// Device bytes a job holds while it runs: four label buffers, the degree
-// histogram, the CSR, the node order and the small state.
+// Device bytes a job holds while it runs (mocd_job_footprint).
 int64_t footprint(int64_t n, int64_t nnz, int32_t pop)
 {
-    const int64_t W = (pop + 3) & ~3;
-    return 4 * n * W * 4 + W * n * 4 + (n + 1) * 4 + nnz * 4 + n * 4 + (1 << 16);
+    int64_t b = 0;
+    mocd_job_footprint(n, nnz, pop, &b);
+    return b;
 }
 
 }  // namespace
@@ -135,6 +136,14 @@ void round_locked(mocd_server *s, std::unique_lock<std::mutex> &lock)
             ++k;
             continue;
         }
+        if (j->issue_error != MOCD_OK) {
+            // A generation or the completion marker could not be issued: the
+            // population did not reach its last generation, so the job fails
+            // (its stream is drained before the context is released).
+            finish(s, j, kFailed, j->issue_error);
+            s->running.erase(s->running.begin() + k);
+            continue;
+        }
         const cudaError_t q = cudaEventQuery(j->done);
         if (q == cudaErrorNotReady) {
             ++k;
@@ -198,7 +207,11 @@ void round_locked(mocd_server *s, std::unique_lock<std::mutex> &lock)
         j->issued += k;
         // Completion marker after the job's last generation, on its own stream.
         if (rc == MOCD_OK && j->issued == j->generations) rc = mocd::record_on_stream(j->ctx, j->done);
-        if (rc) j->issued = j->generations;  // surfaced at retirement
+        if (rc) {
+            // Nothing more is issued; retirement fails the job with this status.
+            j->issue_error = rc;
+            j->issued = j->generations;
+        }
     }
 }
 
@@ -240,6 +253,19 @@ void scheduler(mocd_server *s)
 }  // namespace
 
 extern "C" {
+
+int mocd_job_footprint(int64_t n, int64_t nnz, int32_t pop_size, int64_t *bytes)
+{
+    if (!bytes || n < 1 || nnz < 0 || pop_size < 1 || pop_size > mocd::kMaxPop) return MOCD_ERR_INVALID_ARG;
+    const int64_t W = (pop_size + 3) & ~3;
+    const int64_t labels = 4 * n * W * 4;         // P halves, Q, post-crossover children
+    const int64_t hist = W * n * 4;               // degree histogram
+    const int64_t graph = (n + 1) * 4 + nnz * 4 + n * 4 + 4;  // CSR, node order, symmetry flag
+    const int64_t front = (int64_t)pop_size * n * 4 + 2 * mocd::kMaxPop * 4;  // front download
+    const int64_t fixed = (int64_t)1 << 20;       // small state, graph executable, events
+    *bytes = labels + hist + graph + front + fixed;
+    return MOCD_OK;
+}
 
 int mocd_server_create(mocd_server **out, int64_t hbm_budget_bytes, int32_t max_running, int32_t depth)
 {

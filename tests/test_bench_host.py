@@ -46,13 +46,24 @@ def test_reduce_step_two_ranks_gloo():
 
 
 def test_algorithmic_bytes():
+    """Per-individual model of the method: evaluation 16m + 8n, crossover
+    4 E_S n + 4n, mutation 8n + M_P (16m + 8n), times N_p; the node-major
+    access model beside it."""
     sys.path.insert(0, ROOT)
     import bench
     b = bench.algorithmic_bytes(n=1000, m=5000, np_=100, p_mut=0.2)
+    assert b["evaluate"] == 100 * (16 * 5000 + 8 * 1000)
+    assert b["crossover"] == 100 * (4 * 4 * 1000 + 4 * 1000)
+    assert abs(b["mutation"] - 100 * (8 * 1000 + 0.2 * (16 * 5000 + 8 * 1000))) < 1e-6
+    a = bench.access_bytes(n=1000, m=5000, np_=100, p_mut=0.2)
     csr = 4 * 1001 + 4 * 10000
-    assert b["crossover"] == 16 * 100 * 1000
-    assert b["evaluate"] == 4 * 100 * 1000 + 4 * 100 * 5000 + 8 * 100 * 1000 + csr
-    assert b["mutation"] == 8 * 100 * 1000 + 4 * 0.2 * 100 * 10000 + csr + 4 * 100 * 1000
+    assert a["crossover"] == 16 * 100 * 1000
+    assert a["evaluate"] == 4 * 100 * 1000 + 4 * 100 * 5000 + 8 * 100 * 1000 + csr
+    assert a["mutation"] == 8 * 100 * 1000 + 4 * 0.2 * 100 * 10000 + csr + 4 * 100 * 1000
+    r = bench.kernel_roofline("mutation", 0.5, 1000, 5000, 100, 0.2, 1000.0, "measured", "none")
+    assert abs(r["achieved"] - b["mutation"] / 0.5e-3 / 1e9) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 1000.0) < 1e-12
+    assert abs(r["frac_access"] - a["mutation"] / 0.5e-3 / 1e9 / 1000.0) < 1e-12
 
 
 def test_recorded_traffic_only_for_the_current_source(tmp_path, monkeypatch):

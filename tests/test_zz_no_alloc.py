@@ -7,10 +7,11 @@ synchronisation). mocd_evaluate_noalloc serves them with a fixed scratch array
 compiled into the library. This test calls it through the C ABI on device
 buffers and checks it against the allocating entry point mocd_evaluate, bit
 for bit, on two calls in a row (the second with a different size, so stale
-scratch from the first call would show up)."""
+scratch from the first call would show up), and against the CPU oracle."""
 import numpy as np
 import pytest
 
+import oracle
 import paper_2506_01752_gb300 as mocd
 import synth
 
@@ -56,6 +57,10 @@ def test_noalloc_matches_evaluate_on_two_calls():
             ref_intra, ref_sumsq = mocd.evaluate(ctx, lab)
             assert np.array_equal(d_intra.cpu().numpy(), ref_intra)
             assert np.array_equal(d_sumsq.cpu().numpy(), ref_sumsq)
+            # and directly against the CPU oracle's exact objectives
+            orc_intra, orc_sumsq = oracle.objectives(rp, ci, lab)
+            assert np.array_equal(d_intra.cpu().numpy(), orc_intra)
+            assert np.array_equal(d_sumsq.cpu().numpy(), orc_sumsq)
     finally:
         mocd.destroy(ctx)
 
