@@ -80,7 +80,7 @@ def test_server_results_equal_alone(budget, max_running, background):
 
 
 def test_server_failures():
-    srv = mocd.Server(1 << 20, max_running=4, depth=2)  # 1 MiB
+    srv = mocd.Server(2 << 20, max_running=4, depth=2)  # 2 MiB: the small jobs fit, planted-1k does not
     try:
         big_rp, big_ci, _ = synth.workload("planted-1k", seed=0)
         j_big = srv.submit(big_rp, big_ci, mocd.Params(), 5)          # footprint > budget
