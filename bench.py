@@ -138,10 +138,12 @@ def access_bytes(n: int, m: int, np_: int, p_mut: float) -> dict:
     return {
         # P half + Q rows in, next P + children rows out
         "crossover": 16 * W * n,
-        # own row in, Q row out, each selected pair's neighbour labels, CSR, clearing the D_c histogram
-        "mutation": 8 * W * n + 4 * p_mut * np_ * 2 * m + csr + 4 * np_ * n,
-        # own rows, one neighbour row per undirected edge (from its lower end), D_c read-modify-write, CSR
-        "evaluate": 4 * W * n + 4 * W * m + 8 * np_ * n + csr,
+        # own row in, Q row out, each selected pair's neighbour labels, CSR, and the degree-histogram
+        # additions of every child's final label (read-modify-write of a 4-byte cell)
+        "mutation": 8 * W * n + 4 * p_mut * np_ * 2 * m + csr + 8 * np_ * n,
+        # own rows, one neighbour row per undirected edge (from its lower end), CSR, and the sweep
+        # of the [n][W] degree histogram that forms sum_c D_c^2
+        "evaluate": 4 * W * n + 4 * W * m + csr + 4 * W * n,
         "select": 0,
     }
 

@@ -729,20 +729,11 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
     const int4 *__restrict__ C4 = reinterpret_cast<const int4 *>(child);
     int4 *__restrict__ Q4 = reinterpret_cast<int4 *>(q);
 
-    // The evaluation that follows accumulates into hist and acc: clear them
-    // here, overlapped with this compute-bound kernel.
-    {
-        const size_t words = (size_t)W * (size_t)gp.n;
-        uint4 *h4 = reinterpret_cast<uint4 *>(hist);
-        const size_t n4 = words >> 2;
-        for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n4; t += (size_t)gridDim.x * blockDim.x)
-            h4[t] = make_uint4(0, 0, 0, 0);
-        for (size_t t = (n4 << 2) + blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < words;
-             t += (size_t)gridDim.x * blockDim.x)
-            hist[t] = 0;
-        if (blockIdx.x == 0)
-            for (int t = threadIdx.x; t < 2 * kMaxPop; t += blockDim.x) acc[t] = 0;
-    }
+    // The evaluation that follows accumulates into acc: clear it here. The
+    // histogram is zero on entry (the previous evaluation's square sweep
+    // cleared it) and receives D below.
+    if (blockIdx.x == 0)
+        for (int t = threadIdx.x; t < 2 * kMaxPop; t += blockDim.x) acc[t] = 0;
 
     // Nodes in degree-descending order: every warp starts with one of the
     // costliest nodes, which balances the grid-stride loop.
@@ -991,7 +982,20 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
             if (active) out = reinterpret_cast<const int4 *>(s_res)[lane];
             __syncwarp();
         }
-        if (active) Q4[(size_t)v * nq + lane] = out;
+        if (active) {
+            Q4[(size_t)v * nq + lane] = out;
+            // D of the evaluation's degree histogram: every child's final label
+            // of v gets deg(v) (label-major cell label * W + child). The old
+            // value is not needed, so these are reductions that do not stall.
+            if (deg > 0) {
+                const int i0 = 4 * lane;
+                const unsigned d = (unsigned)deg;
+                if (i0 + 0 < np) atomicAdd(hist + (size_t)out.x * W + i0 + 0, d);
+                if (i0 + 1 < np) atomicAdd(hist + (size_t)out.y * W + i0 + 1, d);
+                if (i0 + 2 < np) atomicAdd(hist + (size_t)out.z * W + i0 + 2, d);
+                if (i0 + 3 < np) atomicAdd(hist + (size_t)out.w * W + i0 + 3, d);
+            }
+        }
     }
 }
 

@@ -49,7 +49,7 @@ struct PopState {
     int32_t *buf[2];          // P halves [n][W]: the P of R is buf[(g + 1) & 1]
     int32_t *q;               // Q [n][W]
     int32_t *c;               // post-crossover children [n][W]
-    uint32_t *hist;           // [n][W] label-major D of (individual, label)
+    uint32_t *hist;           // [n][W] label-major D of (individual, label); zero between evaluations
     unsigned long long *acc;  // [2][kMaxPop]: intra (undirected edges), S
     int64_t *pk;              // [2][kMaxPop]: P keys k1 (m - intra), k2 (S), P order
     int64_t *rk;              // [2][2 kMaxPop]: R keys (P then Q) of the last selection
@@ -118,6 +118,15 @@ cudaError_t launch_symmetry_check(int n, const int32_t *row_ptr, const int32_t *
 // Occupancy-derived grid sizes.
 // Resident blocks of the evaluation kernel in the given histogram layout.
 int grid_for_eval(int sms, bool label_major = true);
+int grid_for_eval_intra(int sms);
+int grid_for_square_sum(int sms);
+// Objectives of the offspring inside a generation: the mutation kernel has
+// already added every child's degrees to the label-major histogram (and
+// cleared acc); this counts intra, then forms S from the histogram and zeroes
+// it.
+cudaError_t launch_evaluate_offspring(int n, int W, int count, const int32_t *row_ptr, const int32_t *col_idx,
+                                      const int32_t *labels, uint32_t *hist, unsigned long long *acc,
+                                      int grid, int sq_grid, cudaStream_t s, const int32_t *order);
 int grid_for_crossover(int sms, int es);
 int grid_for_mutation(int sms, int hash_size, int *smem_bytes);
 int mutation_warps_per_block();

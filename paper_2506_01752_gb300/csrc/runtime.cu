@@ -2,7 +2,8 @@
 //
 // A context owns the uploaded CSR, the population buffers (node-major label
 // rows, see mocd_internal.h) and one CUDA graph that runs a whole generation
-// of Alg. 1: crossover -> mutation -> clear histogram -> evaluate -> select.
+// of Alg. 1: crossover -> mutation (which also builds the degree histogram of
+// the offspring) -> evaluate -> select.
 // Every kernel reads the generation number from device memory, so the same
 // graph is replayed for every generation with no host work in between.
 #include <algorithm>
@@ -50,7 +51,9 @@ struct mocd_ctx {
     size_t hist_cap = 0;    // entries of ps.hist
     void *d_small = nullptr;
     int grid_eval = 0, grid_cross = 0, grid_mut = 0;
+    int grid_eval_intra = 0, grid_square = 0;
     int occ_eval = 0, occ_cross = 0, occ_mut = 0;  // occupancy-limited grids
+    int occ_eval_intra = 0, occ_square = 0;
     int nodes_per_warp = 1;                         // launch shape (autotuned for batches)
     int32_t host_gen = 0;   // generations run since init
     int32_t version = 0;    // bumped whenever the population is (re)built
@@ -182,6 +185,8 @@ void size_grids(mocd_ctx *c)
         return (int)std::max<long long>(1, std::min<long long>(occ, want));
     };
     c->grid_eval = shape(c->occ_eval, kBlock / 32);
+    c->grid_eval_intra = shape(c->occ_eval_intra, kBlock / 32);
+    c->grid_square = shape(c->occ_square, kBlock / 32);
     c->grid_cross = shape(c->occ_cross, kBlock / 32);
     c->grid_mut = shape(c->occ_mut, mutation_warps_per_block());
 }
@@ -271,6 +276,8 @@ int prepare_population(mocd_ctx *c, const mocd_params *p)
     gp.thr_c = (unsigned long long)floor(p->p_crossover * 4294967296.0);
     gp.thr_m = (unsigned long long)floor(p->p_mutation * 4294967296.0);
     c->occ_eval = grid_for_eval(c->sms);
+    c->occ_eval_intra = grid_for_eval_intra(c->sms);
+    c->occ_square = grid_for_square_sum(c->sms);
     c->occ_cross = grid_for_crossover(c->sms, gp.es);
     int smem = 0;
     c->occ_mut = grid_for_mutation(c->sms, gp.hash_size, &smem);
@@ -292,7 +299,8 @@ cudaError_t mark(mocd_ctx *c, int k, cudaStream_t st)
 }
 
 // One generation of Alg. 1 on stream st. The mutation kernel also clears the
-// histogram and accumulators that the evaluation then fills.
+// accumulators and adds the offspring's degrees to the histogram that the
+// evaluation then squares (and zeroes).
 int issue_generation(mocd_ctx *c, cudaStream_t st, bool events)
 {
     const GenParams &gp = c->gp;
@@ -302,8 +310,8 @@ int issue_generation(mocd_ctx *c, cudaStream_t st, bool events)
     if (events) CK(mark(c, 1, st));
     CK(launch_mutation(gp, ps, c->d_row_ptr, c->d_col_idx, c->d_order, c->grid_mut, st));
     if (events) CK(mark(c, 2, st));
-    CK(launch_evaluate(gp.n, gp.W, gp.np, c->d_row_ptr, c->d_col_idx, ps.q, ps.hist, ps.acc,
-                       c->grid_eval, st, c->d_order));
+    CK(launch_evaluate_offspring(gp.n, gp.W, gp.np, c->d_row_ptr, c->d_col_idx, ps.q, ps.hist, ps.acc,
+                                 c->grid_eval_intra, c->grid_square, st, c->d_order));
     if (events) CK(mark(c, 3, st));
     CK(launch_select(gp, ps, 1, st));
     if (events) CK(mark(c, 4, st));
@@ -340,6 +348,8 @@ int start_population(mocd_ctx *c, uint32_t base_gen)
     if (rc) return rc;
     CK(launch_evaluate(gp.n, gp.W, gp.np, c->d_row_ptr, c->d_col_idx, phalf, ps.hist, ps.acc,
                        c->grid_eval, c->stream));
+    // Generations expect a zero histogram (the mutation kernel adds into it).
+    CK(cudaMemsetAsync(ps.hist, 0, (size_t)gp.W * (size_t)gp.n * sizeof(uint32_t), c->stream));
     c->gen_host_value = base_gen;
     CK(cudaMemcpyAsync(ps.gen, &c->gen_host_value, sizeof(uint32_t), cudaMemcpyHostToDevice, c->stream));
     CK(launch_select(gp, ps, 0, c->stream));

@@ -425,3 +425,26 @@ def test_full_size_1m_sampled():
         Q, rk1, rk2 = oracle.make_offspring_range(rp, ci, op, 1, st, i, i + 1)
         assert np.array_equal(q[i], Q[i]), f"child {i} differs"
         assert qk1[i] == rk1[i] and qk2[i] == rk2[i]
+
+
+@pytest.mark.parametrize("n,kw,G", [
+    (200_000, dict(pop_size=100, seed=2), 2),
+    (170_000, dict(pop_size=128, n_parents=5, seed=3), 1),     # the widest population
+    (400_000, dict(pop_size=50, seed=4, init_mode=1), 1),      # W = 52: a partial last int4
+])
+def test_label_matrix_beyond_l2_matches_oracle(n, kw, G):
+    """Label matrices and degree histograms larger than half the L2 (so the
+    histogram additions of the first generations miss it): initial
+    population and whole generations bit-exact against the oracle, with
+    populations of 100, 128 and 50 (a partial last int4 of labels)."""
+    rp, ci, _ = synth.lfr_style(n, 16, 120, 0.3, cmin=20, cmax=1000, seed=n)
+    assert ((kw["pop_size"] + 3) // 4 * 4) * n * 4 > 64 << 20
+    gp, op = _params(**kw)
+    m = int(rp[-1] // 2)
+    ref = oracle.population_init(rp, ci, op)
+    with Ctx(rp, ci) as h:
+        mocd.population_init(h, gp)
+        _compare_state(h, ref, m)
+        mocd.generation(h, G)
+        ref = oracle.run_parallel(rp, ci, op, ref, G)
+        _compare_state(h, ref, m)
