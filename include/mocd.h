@@ -308,13 +308,16 @@ void mocd_batch_destroy(mocd_batch *b);
  *                       policy 1 admits the queued job with the least work
  *                       ((n + 2m) x (G + 1)) first.
  * Calls on one server may come from any host thread.
- *   mocd_job_footprint  the device bytes the server accounts for a job while
- *                       it runs (admission compares their sum with the budget):
+ *   mocd_job_footprint  the device bytes the server accounts for a job on the
+ *                       graph with host row pointers row_ptr[n + 1] while it
+ *                       runs (admission compares their sum with the budget):
  *                       the four label buffers and the degree histogram
  *                       (5 x 4 n W bytes, W = N_p rounded up to a multiple of
- *                       4), the CSR and node order, the individual-major
- *                       buffer of the front download (4 n N_p) and 1 MiB of
- *                       small state. Errors: INVALID_ARG.
+ *                       4), the CSR and node order, the mutation's per-node
+ *                       hints (4 n) and deferred-vote list (8 N_p per node of
+ *                       degree 33..128), the individual-major buffer of the
+ *                       front download (4 n N_p) and 1 MiB of small state.
+ *                       Errors: INVALID_ARG.
  */
 typedef struct mocd_server mocd_server;
 int mocd_server_create(mocd_server **out, int64_t hbm_budget_bytes, int32_t max_running, int32_t depth);
@@ -326,7 +329,7 @@ int mocd_server_job_state(mocd_server *s, int64_t job_id, int32_t *state, int32_
 int mocd_server_result(mocd_server *s, int64_t job_id, int32_t cap, int32_t *count, int32_t *labels,
                        double *f1, double *f2, int64_t *intra, int64_t *sumsq, int32_t *best);
 void mocd_server_destroy(mocd_server *s);
-int mocd_job_footprint(int64_t n, int64_t nnz, int32_t pop_size, int64_t *bytes);
+int mocd_job_footprint(int64_t n, const int64_t *row_ptr, int32_t pop_size, int64_t *bytes);
 
 /*
  * Test support (not a step of the method): host-side failure injection, so

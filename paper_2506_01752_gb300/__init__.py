@@ -121,7 +121,7 @@ def load():
         "mocd_server_job_state": (ctypes.c_int, [P, i64, P, P]),
         "mocd_server_result": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, P]),
         "mocd_server_destroy": (None, [P]),
-        "mocd_job_footprint": (ctypes.c_int, [i64, i64, i32, P]),
+        "mocd_job_footprint": (ctypes.c_int, [i64, P, i32, P]),
         "mocd_debug_inject": (ctypes.c_int, [i32, i32, i32, i32]),
         "mocd_debug_pool_usage": (ctypes.c_int, [i32, P, P]),
     }
@@ -378,10 +378,11 @@ class Server:
             self.h.value = None
 
 
-def job_footprint(n: int, nnz: int, pop_size: int = 100) -> int:
-    """Device bytes the server accounts for a job while it runs."""
+def job_footprint(row_ptr, pop_size: int = 100) -> int:
+    """Device bytes the server accounts for a job on this graph while it runs."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
     out = ctypes.c_int64()
-    _check(load().mocd_job_footprint(int(n), int(nnz), int(pop_size), ctypes.byref(out)), "mocd_job_footprint")
+    _check(load().mocd_job_footprint(rp.size - 1, _p(rp), int(pop_size), ctypes.byref(out)), "mocd_job_footprint")
     return out.value
 
 

@@ -158,8 +158,11 @@ __global__ void __launch_bounds__(kBlock)
 crossover_kernel(GenParams gp, const int32_t *buf0, const int32_t *buf1, int32_t *out0, int32_t *out1,
                  const int32_t *__restrict__ q, int32_t *__restrict__ child,
                  const int32_t *__restrict__ keep, const int32_t *__restrict__ par_r,
-                 const int32_t *__restrict__ copy_r, const uint32_t *__restrict__ gen_ptr)
+                 const int32_t *__restrict__ copy_r, const uint32_t *__restrict__ gen_ptr,
+                 int *__restrict__ dcount)
 {
+    // The mutation kernel that follows appends deferred pairs from zero.
+    if (blockIdx.x == 0 && threadIdx.x < 2) dcount[threadIdx.x] = 0;
     extern __shared__ int smem[];
     const int W = gp.W, np = gp.np, E = gp.es;
     const int nq = W >> 2;
@@ -319,23 +322,25 @@ crossover_kernel(GenParams gp, const int32_t *buf0, const int32_t *buf1, int32_t
 }
 
 // ---------------------------------------------------------------------------
-// Mutation. Node v of child i mutates iff its MCOIN word is below thr_m and
-// deg(v) > 0; it then takes the most frequent label among its neighbours in
-// the post-crossover child (synchronous: all reads come from `child`), the
-// tie among the t most frequent labels broken by the MTIE word (the
-// pick(u, t)-th smallest). A warp takes a node; its lanes take the node's
-// selected children. Each lane summarises its pair's neighbour labels with a
-// three-counter Misra-Gries pass and recounts the survivors exactly, which
-// settles the pair whenever the best count c has 4 c > deg. The other pairs
-// get an exact vote. Degree <= 32: when many pairs of the node are left (the
-// first generations, while the labels are still nearly all distinct), each
-// lane sorts its own pair's labels in registers with an odd-even merge
-// network of 8, 16 or 32 entries and reads the tied labels off the runs;
-// when few are left, the whole warp votes on two pairs at a time (one
-// neighbour per lane grouped by __match_any_sync, the pick(u, t)-th tied
-// label by removing minima or, for deep ranks, by sorting the tied labels
-// across the warp). Degree 33..64: a sorting network over two labels per
-// lane. Beyond: a count table in shared memory.
+// Mutation (Sec. 4.3.2). Node v of child i mutates iff its MCOIN word is
+// below thr_m and deg(v) > 0; it then takes the most frequent label among its
+// neighbours in the post-crossover child (synchronous: all reads come from
+// `child`), the tie among the t most frequent labels broken by the MTIE word
+// (the pick(u, t)-th smallest). A warp takes a node; its lanes take the
+// node's selected children, whose neighbour labels are staged into a
+// per-warp tile (a column per pair). Degree <= 32: when many pairs are
+// selected, each lane sorts its own pair's labels in registers with an
+// odd-even merge network of 8, 16 or 32 entries and reads the tied labels
+// off the runs, all pairs at once; when few are, the whole warp votes on two
+// pairs at a time (one neighbour per lane grouped by __match_any_sync, the
+// pick(u, t)-th tied label by removing minima or, for deep ranks, by sorting
+// the tied labels across the warp). Degree > 32: when the node's history says
+// it pays, a three-counter Misra-Gries summary and an exact recount of its
+// survivors settle every pair whose best count c has 4 c > deg (every label
+// reaching c is then a candidate); the other pairs of degree 33..kDeferMax
+// are listed for mutation_vote_kernel (one pair per thread, labels sorted in
+// registers), and those of higher degree take a count table in shared
+// memory, one pair at a time.
 // ---------------------------------------------------------------------------
 
 // The ka-th and kb-th smallest of the distinct labels held by the lanes of
@@ -411,6 +416,7 @@ __device__ __forceinline__ void cp_async_wait_all()
 
 constexpr int kTileStride = 33;  // padded row of the per-warp label tile
 constexpr int kTileRows = 32;    // neighbours whose labels the tile keeps
+static_assert(kDeferMax == 4 * kTileRows, "deferred classes: degrees 33..64 and 65..128");
 constexpr int kMutBlock = 128;   // mutation threads per block (shared memory bound)
 
 // Batcher's odd-even merge sort of x[0, N) (N a power of two), ascending,
@@ -477,7 +483,7 @@ __device__ __forceinline__ void sort_network(int (&x)[N])
 // labels then form runs, the longest runs are the tied labels in ascending
 // order, and the pick(u, t)-th of them is the result.
 template <int N>
-__device__ __forceinline__ int lane_mode(const int *col, int deg, uint32_t u)
+__device__ __forceinline__ int lane_mode(const int *col, int deg, uint32_t u, int &best_count)
 {
     int x[N];
 #pragma unroll
@@ -497,6 +503,7 @@ __device__ __forceinline__ int lane_mode(const int *col, int deg, uint32_t u)
         }
         if (last && run == best) ends |= 1u << j;
     }
+    best_count = best;
     const int t = __popc(ends);
     const unsigned kk = t > 1 ? pick_index(u, (uint32_t)t) : 0u;
     // Position of the kk-th set bit of `ends`, halving the window each step.
@@ -521,9 +528,11 @@ __device__ __forceinline__ int lane_mode(const int *col, int deg, uint32_t u)
 }
 
 // Lane-parallel exact vote of every unresolved pair of a node with
-// deg <= kTileRows; unresolved lanes write their result.
+// deg <= kTileRows; unresolved lanes write their result. Returns, for the
+// lane's pair, whether its best count c has 4 c > deg (the pairs the
+// Misra-Gries pass would have settled).
 template <int N>
-__device__ __forceinline__ void lane_votes(const int *tile, int deg, bool mine, int i, uint4 tw, int *s_res)
+__device__ __forceinline__ bool lane_votes(const int *tile, int deg, bool mine, int i, uint4 tw, int *s_res)
 {
     const int src = i >> 2;
     const uint32_t w0 = __shfl_sync(0xffffffffu, tw.x, src);
@@ -532,73 +541,13 @@ __device__ __forceinline__ void lane_votes(const int *tile, int deg, bool mine, 
     const uint32_t w3 = __shfl_sync(0xffffffffu, tw.w, src);
     const int k = i & 3;
     const uint32_t u = k == 0 ? w0 : (k == 1 ? w1 : (k == 2 ? w2 : w3));
-    if (mine) s_res[i] = lane_mode<N>(tile + (threadIdx.x & 31), deg, u);
+    int best = 0;
+    if (mine) s_res[i] = lane_mode<N>(tile + (threadIdx.x & 31), deg, u, best);
+    return mine && 4 * best > deg;
 }
 
-// Exact neighbour-majority of one pair whose node has 32 < deg <= 64: the
-// labels (two per lane: neighbour j = lane from the tile, 32 + lane from
-// global memory, INT_MAX beyond deg) are sorted across the warp with a
-// bitonic network; equal labels then form runs, whose lengths come from the
-// ballot of run starts. The tied runs of the largest length are already in
-// ascending label order, so the pick(u, t)-th of them is found by rank.
-__device__ __forceinline__ int warp_mode_sort64(const GenParams &gp, const int32_t *__restrict__ child,
-                                                const int32_t *__restrict__ col_idx, int beg, int deg,
-                                                const int *tile_col, int i, uint32_t tie_u)
-{
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    int a = tile_col[lane * kTileStride];
-    int b = 32 + lane < deg ? child[(size_t)__ldg(col_idx + beg + 32 + lane) * gp.W + i] : INT_MAX;
-    // Element e = lane holds a, e = 32 + lane holds b; ascending bitonic sort.
-#pragma unroll
-    for (int k = 2; k <= 64; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            if (j == 32) {
-                const int lo = min(a, b), hi = max(a, b);
-                a = lo;
-                b = hi;
-            } else {
-                const int pa = __shfl_xor_sync(kFull, a, j);
-                const int pb = __shfl_xor_sync(kFull, b, j);
-                const bool lower = (lane & j) == 0;
-                const bool asc_a = (lane & k) == 0;
-                const bool asc_b = ((lane + 32) & k) == 0;
-                a = (lower == asc_a) ? min(a, pa) : max(a, pa);
-                b = (lower == asc_b) ? min(b, pb) : max(b, pb);
-            }
-        }
-    }
-    // Run starts among the deg real elements (the padding sorts last).
-    const int prev_a = __shfl_up_sync(kFull, a, 1);
-    const int prev_b = __shfl_up_sync(kFull, b, 1);
-    const int last_a = __shfl_sync(kFull, a, 31);
-    const bool sa = lane < deg && (lane == 0 || a != prev_a);
-    const bool sb = 32 + lane < deg && (lane == 0 ? b != last_a : b != prev_b);
-    const unsigned long long starts =
-        ((unsigned long long)__ballot_sync(kFull, sb) << 32) | (unsigned long long)__ballot_sync(kFull, sa);
-    auto run_length = [&](int e) {
-        const unsigned long long after = e < 63 ? starts >> (e + 1) : 0ull;
-        return (after ? e + __ffsll((long long)after) : deg) - e;
-    };
-    const int ca = sa ? run_length(lane) : 0;
-    const int cb = sb ? run_length(32 + lane) : 0;
-    const int mx = (int)__reduce_max_sync(kFull, (unsigned)max(ca, cb));
-    const unsigned ta = __ballot_sync(kFull, ca == mx);
-    const unsigned tb = __ballot_sync(kFull, cb == mx);
-    const int na = __popc(ta);
-    const int t = na + __popc(tb);
-    const int kk = t > 1 ? (int)pick_index(tie_u, (uint32_t)t) : 0;
-    if (kk < na) {
-        const unsigned w = __ballot_sync(kFull, ((ta >> lane) & 1u) && __popc(ta & lt) == kk);
-        return __shfl_sync(kFull, a, __ffs(w) - 1);
-    }
-    const unsigned w = __ballot_sync(kFull, ((tb >> lane) & 1u) && __popc(tb & lt) == kk - na);
-    return __shfl_sync(kFull, b, __ffs(w) - 1);
-}
-
-// Exact neighbour-majority of one pair of a node with degree > 64 by the
-// whole warp: a per-warp open-addressing
+// Exact neighbour-majority of one pair of a node with degree > kDeferMax by
+// the whole warp: a per-warp open-addressing
 // count table in shared memory, sized to the node (the
 // smallest power of two with at least 2 deg slots), filled with one insert
 // per distinct label of each 32-neighbour chunk (__match_any_sync gives the
@@ -608,7 +557,8 @@ __device__ __forceinline__ int warp_mode_sort64(const GenParams &gp, const int32
 // bit from the top (deep ranks).
 __device__ __forceinline__ int warp_mode_table(const GenParams &gp, const int32_t *__restrict__ child,
                                             const int32_t *__restrict__ col_idx, int beg, int deg,
-                                            const int *tile_col, int i, int *hkey, int *hcnt, uint32_t tie_u)
+                                            const int *tile_col, int i, int *hkey, int *hcnt, uint32_t tie_u,
+                                            unsigned &best_count)
 {
     const int lane = threadIdx.x & 31;
     const int W = gp.W;
@@ -648,6 +598,7 @@ __device__ __forceinline__ int warp_mode_table(const GenParams &gp, const int32_
     unsigned mx_l = 0;
     for (int s = 0; s < per_lane; ++s) mx_l = max(mx_l, (unsigned)hcnt[lane + 32 * s]);
     const unsigned mx = __reduce_max_sync(kFull, mx_l);
+    best_count = mx;
     unsigned act = 0;
     for (int s = 0; s < per_lane; ++s)
         if ((unsigned)hcnt[lane + 32 * s] == mx) act |= 1u << s;
@@ -709,7 +660,8 @@ __global__ void __launch_bounds__(kMutBlock, 6)
 mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
                 const int32_t *__restrict__ order, const int32_t *__restrict__ child, int32_t *__restrict__ q,
                 const uint32_t *__restrict__ gen_ptr, uint32_t *__restrict__ hist,
-                unsigned long long *__restrict__ acc)
+                unsigned long long *__restrict__ acc, uint32_t *__restrict__ hint, int2 *__restrict__ dlist,
+                int *__restrict__ dcount)
 {
     extern __shared__ int smem[];
     const int W = gp.W, np = gp.np;
@@ -769,7 +721,16 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
             if (active) reinterpret_cast<int4 *>(s_res)[lane] = out;
             __syncwarp();
             const int my_u0 = lane < deg ? __ldg(col_idx + beg + lane) : 0;
-            const int my_u1 = 32 + lane < deg ? __ldg(col_idx + beg + 32 + lane) : 0;
+            // Degree <= kTileRows: the exact per-lane votes below settle all
+            // pairs at once and cost less than the Misra-Gries pass, even once
+            // the population has settled. Above: the pass runs when the last
+            // generation's exact results (whichever path produced them) say
+            // that most of v's pairs had a label above deg / 4, the pairs the
+            // pass settles. hint = (pairs << 16) | such pairs; 0: no history.
+            const uint32_t h = deg > kTileRows ? hint[v] : 0u;
+            const bool use_mg = deg > kTileRows && (h == 0u || 2u * (h & 0xffffu) >= (h >> 16));
+            const bool deferred_class = deg > kTileRows && deg <= kDeferMax;
+            int nsettle = 0;  // pairs of v with 4 (best count) > deg, settled here
             bool have_tw = false;
             uint4 tw = make_uint4(0, 0, 0, 0);
             for (int base = 0; base < nsel; base += 32) {
@@ -798,19 +759,22 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                     c1 = ok && f1 ? x : c1;
                     c2 = ok && f2 ? x : c2;
                 };
-                const int dt = min(deg, kTileRows);
+                // The tile is read by the pass and by the votes of degree <= 32
+                // and > kDeferMax; pairs of the deferred degrees need it only
+                // for the pass.
+                const int dt = (use_mg || !deferred_class) ? min(deg, kTileRows) : 0;
                 for (int j = 0; j < dt; ++j) {
-                    const int u = __shfl_sync(kFull, j < 32 ? my_u0 : my_u1, j & 31);
+                    const int u = __shfl_sync(kFull, my_u0, j);
                     if (has) cp_async4(tile + j * kTileStride + lane, child + (size_t)u * W + i);
                 }
                 cp_async_wait_all();
                 __syncwarp();
-                if (has) {
+                if (has && use_mg) {
 #pragma unroll 4
                     for (int j = 0; j < dt; ++j) mg(tile[j * kTileStride + lane], true);
                 }
                 // Neighbours beyond the tile: global loads, eight in flight.
-                for (int e0 = kTileRows; e0 < deg; e0 += 32) {
+                for (int e0 = kTileRows; use_mg && e0 < deg; e0 += 32) {
                     const int my_u = e0 + lane < deg ? __ldg(col_idx + beg + e0 + lane) : 0;
                     const int cnt = min(32, deg - e0);
                     for (int j0 = 0; j0 < cnt; j0 += 8) {
@@ -829,15 +793,7 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                 // (nor the -1 padding below) can have, so it counts 0.
                 const int s0 = n0 > 0 ? c0 : -2, s1 = n1 > 0 ? c1 : -3, s2 = n2 > 0 ? c2 : -4;
                 int h0 = 0, h1 = 0, h2 = 0;
-                if (has && deg <= kTileRows) {
-                    for (int j = 0; j < deg; ++j) {
-                        const int x = tile[j * kTileStride + lane];
-                        h0 += x == s0;
-                        h1 += x == s1;
-                        h2 += x == s2;
-                    }
-                }
-                if (deg > kTileRows) {
+                if (use_mg) {
                     // The first kTileRows labels are still in the tile.
                     if (has) {
 #pragma unroll 4
@@ -870,7 +826,7 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                 // If the best candidate count c satisfies 4 c > deg, every label
                 // reaching c is a candidate: the tied set is complete and exact.
                 const int best = max(h0, max(h1, h2));
-                const bool done = has && 4 * best > deg;
+                const bool done = has && use_mg && 4 * best > deg;
                 if (done) {
                     // Tied candidates in ascending order, then the MTIE pick.
                     int a = h0 == best ? s0 : INT_MAX;
@@ -893,6 +849,27 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                 }
                 __syncwarp();
                 unsigned rest = __ballot_sync(kFull, has && !done);
+                nsettle += __popc(__ballot_sync(kFull, done));
+                if (rest && deferred_class) {
+                    // Degrees kTileRows + 1 .. kDeferMax: the exact vote of every
+                    // remaining pair runs in mutation_vote_kernel, one pair per
+                    // thread with its labels sorted in registers. Its slot of
+                    // the row holds -1 until then.
+                    const int cls = deg <= 2 * kTileRows ? 0 : 1;
+                    int first = 0;
+                    if (lane == 0) first = atomicAdd(dcount + cls, __popc(rest));
+                    first = __shfl_sync(kFull, first, 0);
+                    if ((rest >> lane) & 1u) {
+                        const int at_list = first + __popc(rest & ((1u << lane) - 1u));
+                        // The capacity is the class's nodes x N_p, every pair
+                        // a generation can defer: the check only keeps a
+                        // corrupted count in bounds.
+                        const int cap = cls ? gp.defer_cap[1] : gp.defer_cap[0];
+                        if (at_list < cap) dlist[(cls ? gp.defer_cap[0] : 0) + at_list] = make_int2(v, i);
+                        s_res[i] = -1;
+                    }
+                    rest = 0;
+                }
                 if (rest && !have_tw) {
                     tw = tie_words(gp, v, lane, g);
                     have_tw = true;
@@ -902,16 +879,18 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                     // with a sorting network (all pairs at once).
                     const int nrest = __popc(rest);
                     const bool mine = (rest >> lane) & 1u;
+                    bool settles = false;
                     if (deg <= 8 && nrest >= 2) {
-                        lane_votes<8>(tile, deg, mine, i, tw, s_res);
+                        settles = lane_votes<8>(tile, deg, mine, i, tw, s_res);
                         rest = 0;
                     } else if (deg > 8 && deg <= 16 && nrest >= 5) {
-                        lane_votes<16>(tile, deg, mine, i, tw, s_res);
+                        settles = lane_votes<16>(tile, deg, mine, i, tw, s_res);
                         rest = 0;
                     } else if (deg > 16 && nrest >= 10) {
-                        lane_votes<32>(tile, deg, mine, i, tw, s_res);
+                        settles = lane_votes<32>(tile, deg, mine, i, tw, s_res);
                         rest = 0;
                     }
+                    nsettle += __popc(__ballot_sync(kFull, settles));
                 }
                 if (deg <= kTileRows) {
                     // Exact vote by the whole warp (lane = neighbour), two
@@ -963,21 +942,25 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                             s_res[ia] = ra;
                             if (two) s_res[ib] = rb;
                         }
+                        nsettle += (4 * (int)ma > deg ? 1 : 0) + ((two && 4 * (int)mb > deg) ? 1 : 0);
                     }
                 }
+                // Degree > kDeferMax: a shared count table, one pair at a time.
                 while (rest) {
                     const int l = __ffs(rest) - 1;
                     rest &= rest - 1;
                     const int ic = __shfl_sync(kFull, i, l);
                     const uint32_t u = __shfl_sync(kFull, word_of(tw, ic & 3), ic >> 2);
-                    const int lab = deg <= 64
-                                        ? warp_mode_sort64(gp, child, col_idx, beg, deg, tile + l, ic, u)
-                                        : warp_mode_table(gp, child, col_idx, beg, deg, tile + l, ic, hkey, hcnt, u);
+                    unsigned mx = 0;
+                    const int lab = warp_mode_table(gp, child, col_idx, beg, deg, tile + l, ic, hkey, hcnt, u, mx);
                     if (lane == 0) s_res[ic] = lab;
+                    nsettle += 4 * (int)mx > deg ? 1 : 0;
                 }
                 __syncwarp();
             }
             __syncwarp();
+            // The deferred pairs add theirs in mutation_vote_kernel.
+            if (lane == 0 && deg > kTileRows) hint[v] = ((uint32_t)nsel << 16) | (uint32_t)nsettle;
             // s_res holds the unselected children's labels and the results.
             if (active) out = reinterpret_cast<const int4 *>(s_res)[lane];
             __syncwarp();
@@ -987,15 +970,107 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
             // D of the evaluation's degree histogram: every child's final label
             // of v gets deg(v) (label-major cell label * W + child). The old
             // value is not needed, so these are reductions that do not stall.
+            // A deferred pair (-1) gets its label and its addition from
+            // mutation_vote_kernel.
             if (deg > 0) {
                 const int i0 = 4 * lane;
                 const unsigned d = (unsigned)deg;
-                if (i0 + 0 < np) atomicAdd(hist + (size_t)out.x * W + i0 + 0, d);
-                if (i0 + 1 < np) atomicAdd(hist + (size_t)out.y * W + i0 + 1, d);
-                if (i0 + 2 < np) atomicAdd(hist + (size_t)out.z * W + i0 + 2, d);
-                if (i0 + 3 < np) atomicAdd(hist + (size_t)out.w * W + i0 + 3, d);
+                if (i0 + 0 < np && out.x >= 0) atomicAdd(hist + (size_t)out.x * W + i0 + 0, d);
+                if (i0 + 1 < np && out.y >= 0) atomicAdd(hist + (size_t)out.y * W + i0 + 1, d);
+                if (i0 + 2 < np && out.z >= 0) atomicAdd(hist + (size_t)out.z * W + i0 + 2, d);
+                if (i0 + 3 < np && out.w >= 0) atomicAdd(hist + (size_t)out.w * W + i0 + 3, d);
             }
         }
+    }
+}
+
+// The exact neighbour-majority of one deferred pair (node of degree
+// kTileRows + 1 .. N) per thread: the pair's labels are gathered into
+// registers (INT_MAX beyond the degree), sorted by the odd-even merge
+// network, and the pick(u, t)-th of the t longest runs is the result, u the
+// MTIE word. The thread writes the label into Q, adds deg(v) to the degree
+// histogram (as the mutation kernel does for the other pairs) and, when the
+// best count c has 4 c > deg, counts the pair in v's hint.
+template <int N>
+__global__ void __launch_bounds__(kMutBlock)
+mutation_vote_kernel(GenParams gp, int cls, const int32_t *__restrict__ row_ptr,
+                     const int32_t *__restrict__ col_idx, const int32_t *__restrict__ child,
+                     int32_t *__restrict__ q, const uint32_t *__restrict__ gen_ptr, uint32_t *__restrict__ hist,
+                     uint32_t *__restrict__ hint, const int2 *__restrict__ dlist, const int *__restrict__ dcount)
+{
+    constexpr int NW = (N + 63) / 64;
+    const uint32_t g = *gen_ptr;
+    const int W = gp.W;
+    const int total = min(dcount[cls], cls ? gp.defer_cap[1] : gp.defer_cap[0]);
+    const int2 *list = dlist + (cls ? gp.defer_cap[0] : 0);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int2 e = list[t];
+        const int v = e.x, i = e.y;
+        const int beg = __ldg(row_ptr + v);
+        const int deg = __ldg(row_ptr + v + 1) - beg;
+        int x[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) x[j] = j < deg ? child[(size_t)__ldg(col_idx + beg + j) * W + i] : INT_MAX;
+        sort_network<N>(x);
+        // The longest run length among the deg real entries and the mask of
+        // the positions where a run of that length ends.
+        int run = 0, best = 0;
+        unsigned long long ends[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) ends[w] = 0ull;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            run = (j > 0 && x[j] == x[j - 1]) ? run + 1 : 1;
+            const bool last = j < deg && (j + 1 == deg || (j + 1 < N && x[j + 1] != x[j]));
+            if (last && run > best) {
+                best = run;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) ends[w] = 0ull;
+            }
+            if (last && run == best) ends[j >> 6] |= 1ull << (j & 63);
+        }
+        int tcount = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) tcount += __popcll(ends[w]);
+        unsigned kk = 0;
+        if (tcount > 1) {
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)v, (uint32_t)(i >> 2), g, kStageMutTie), gp.key0,
+                                          gp.key1);
+            kk = pick_index(word_of(r, i & 3), (uint32_t)tcount);
+        }
+        // Position of the kk-th set bit of the ends mask.
+        int pos = 0;
+        unsigned k = kk;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const unsigned c = (unsigned)__popcll(ends[w]);
+            if (k >= c) {
+                k -= c;
+                continue;
+            }
+            unsigned long long m = ends[w];
+            int p = 64 * w;
+#pragma unroll
+            for (int width = 32; width >= 1; width >>= 1) {
+                const unsigned long long low = m & ((1ull << width) - 1ull);
+                const unsigned lc = (unsigned)__popcll(low);
+                if (k >= lc) {
+                    k -= lc;
+                    m >>= width;
+                    p += width;
+                } else {
+                    m = low;
+                }
+            }
+            pos = p;
+            break;
+        }
+        int res = x[0];
+#pragma unroll
+        for (int j = 1; j < N; ++j) res = pos == j ? x[j] : res;
+        q[(size_t)v * W + i] = res;
+        atomicAdd(hist + (size_t)res * W + i, (unsigned)deg);
+        if (4 * best > deg) atomicAdd(hint + v, 1u);
     }
 }
 
@@ -1038,13 +1113,16 @@ cudaError_t launch_crossover(const GenParams &gp, const PopState &ps, int grid, 
 {
     if (gp.es <= 4)
         crossover_kernel<4><<<grid, kBlock, crossover_smem<4>(), s>>>(
-            gp, ps.buf[0], ps.buf[1], ps.buf[0], ps.buf[1], ps.q, ps.c, ps.keep, ps.par_r, ps.copy_r, ps.gen);
+            gp, ps.buf[0], ps.buf[1], ps.buf[0], ps.buf[1], ps.q, ps.c, ps.keep, ps.par_r, ps.copy_r, ps.gen,
+            ps.dcount);
     else if (gp.es <= 8)
         crossover_kernel<8><<<grid, kBlock, crossover_smem<8>(), s>>>(
-            gp, ps.buf[0], ps.buf[1], ps.buf[0], ps.buf[1], ps.q, ps.c, ps.keep, ps.par_r, ps.copy_r, ps.gen);
+            gp, ps.buf[0], ps.buf[1], ps.buf[0], ps.buf[1], ps.q, ps.c, ps.keep, ps.par_r, ps.copy_r, ps.gen,
+            ps.dcount);
     else
         crossover_kernel<16><<<grid, kBlock, crossover_smem<16>(), s>>>(
-            gp, ps.buf[0], ps.buf[1], ps.buf[0], ps.buf[1], ps.q, ps.c, ps.keep, ps.par_r, ps.copy_r, ps.gen);
+            gp, ps.buf[0], ps.buf[1], ps.buf[0], ps.buf[1], ps.q, ps.c, ps.keep, ps.par_r, ps.copy_r, ps.gen,
+            ps.dcount);
     return cudaGetLastError();
 }
 
@@ -1070,12 +1148,37 @@ int grid_for_mutation(int sms, int hash_size, int *smem_bytes)
     return sms * per_sm;
 }
 
+int grid_for_vote(int sms)
+{
+    int a = 0, b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, mutation_vote_kernel<2 * kTileRows>, kMutBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, mutation_vote_kernel<kDeferMax>, kMutBlock, 0);
+    a = a < 1 ? 1 : a;
+    b = b < 1 ? 1 : b;
+    return sms * (a < b ? a : b);
+}
+
 cudaError_t launch_mutation(const GenParams &gp, const PopState &ps, const int32_t *row_ptr,
-                            const int32_t *col_idx, const int32_t *order, int grid, cudaStream_t s)
+                            const int32_t *col_idx, const int32_t *order, int grid, int vote_grid, cudaStream_t s)
 {
     mutation_kernel<<<grid, kMutBlock, mutation_smem(gp.hash_size), s>>>(gp, row_ptr, col_idx, order, ps.c, ps.q,
-                                                                       ps.gen, ps.hist, ps.acc);
-    return cudaGetLastError();
+                                                                       ps.gen, ps.hist, ps.acc, ps.hint, ps.dlist,
+                                                                       ps.dcount);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (gp.defer_cap[0] > 0) {
+        mutation_vote_kernel<2 * kTileRows><<<vote_grid, kMutBlock, 0, s>>>(gp, 0, row_ptr, col_idx, ps.c, ps.q,
+                                                                           ps.gen, ps.hist, ps.hint, ps.dlist,
+                                                                           ps.dcount);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (gp.defer_cap[1] > 0) {
+        mutation_vote_kernel<kDeferMax><<<vote_grid, kMutBlock, 0, s>>>(gp, 1, row_ptr, col_idx, ps.c, ps.q, ps.gen,
+                                                                        ps.hist, ps.hint, ps.dlist, ps.dcount);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 }  // namespace mocd

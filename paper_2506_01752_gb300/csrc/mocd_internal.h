@@ -36,6 +36,10 @@ bool inject_failure(int site, int *status);
 constexpr int kMaxPop = 128;      // N_p limit: one int4 of labels per lane per row
 constexpr int kMaxParents = 16;   // E_S limit
 constexpr int kBlock = 256;       // threads per block of the node-parallel kernels
+// Mutation votes of nodes with degree 33..kDeferMax that the Misra-Gries
+// pass leaves open run one pair per thread in a second kernel (degree
+// classes 33..64 and 65..128); higher degrees use a per-warp count table.
+constexpr int kDeferMax = 128;
 
 // Random stream stages (third word of the Philox counter is the generation).
 constexpr uint32_t kStageInit = 1;
@@ -61,6 +65,9 @@ struct PopState {
     int32_t *front;           // [2 + kMaxPop]: count, best, members (P positions)
     int64_t *fint;            // [2][kMaxPop]: intra, S of each front member
     double *fval;             // [2][kMaxPop]: f1, f2 of each front member
+    uint32_t *hint;           // [n]: (mutating pairs << 16) | pairs with a label above deg / 4, last generation
+    int2 *dlist;              // deferred mutation votes (node, child): class 0 then class 1
+    int *dcount;              // [2]: deferred votes appended this generation, per class
 };
 
 struct GenParams {
@@ -69,7 +76,8 @@ struct GenParams {
     int np;                   // N_p
     int es;                   // E_S
     int label_bits;           // bits needed for a label in [0, n)
-    int hash_size;            // per-warp hash entries for degree > 32 (0: none)
+    int hash_size;            // per-warp hash entries for degree > kDeferMax (0: none)
+    int defer_cap[2];         // deferred-vote capacity per class: N_p x nodes of the class
     int64_t m;                // edges
     uint32_t key0, key1;      // Philox key (seed)
     unsigned long long thr_c; // crossover iff u <= thr_c
@@ -85,7 +93,8 @@ cudaError_t launch_crossover(const GenParams &gp, const PopState &ps, int grid, 
 // order: the nodes in the sequence the grid-stride loop visits them
 // (degree descending), or NULL for 0..n-1 (evaluation only).
 cudaError_t launch_mutation(const GenParams &gp, const PopState &ps, const int32_t *row_ptr,
-                            const int32_t *col_idx, const int32_t *order, int grid, cudaStream_t s);
+                            const int32_t *col_idx, const int32_t *order, int grid, int vote_grid, cudaStream_t s);
+int grid_for_vote(int sms);
 // hist: label-major [n][W] (label_major) or individual-major [count][n],
 // zeroed by the caller.
 cudaError_t launch_evaluate(int n, int W, int count, const int32_t *row_ptr, const int32_t *col_idx,

@@ -37,6 +37,7 @@ struct mocd_ctx {
 
     int64_t n = 0, m = 0;
     int dmax = 0;
+    int64_t n_defer[2] = {0, 0};  // nodes of degree 33..64 and 65..128 (deferred mutation votes)
     int32_t *d_row_ptr = nullptr;
     int32_t *d_col_idx = nullptr;
     int32_t *d_order = nullptr;   // nodes by degree, descending
@@ -49,9 +50,11 @@ struct mocd_ctx {
     int W = 0;
     size_t pop_cells = 0;   // n * W of the allocated label buffers
     size_t hist_cap = 0;    // entries of ps.hist
+    size_t hint_cap = 0;    // entries of ps.hint
+    size_t dlist_cap = 0;   // entries of ps.dlist
     void *d_small = nullptr;
     int grid_eval = 0, grid_cross = 0, grid_mut = 0;
-    int grid_eval_intra = 0, grid_square = 0;
+    int grid_eval_intra = 0, grid_square = 0, grid_vote = 0;
     int occ_eval = 0, occ_cross = 0, occ_mut = 0;  // occupancy-limited grids
     int occ_eval_intra = 0, occ_square = 0;
     int nodes_per_warp = 1;                         // launch shape (autotuned for batches)
@@ -145,11 +148,15 @@ void free_population(mocd_ctx *c)
     dev_free(c->ps.q, c->stream);
     dev_free(c->ps.c, c->stream);
     dev_free(c->ps.hist, c->stream);
+    dev_free(c->ps.hint, c->stream);
+    dev_free(c->ps.dlist, c->stream);
     dev_free(c->d_small, c->stream);
     c->ps = PopState{};
     c->d_small = nullptr;
     c->pop_cells = 0;
     c->hist_cap = 0;
+    c->hint_cap = 0;
+    c->dlist_cap = 0;
     c->ready = false;
 }
 
@@ -246,14 +253,22 @@ int prepare_population(mocd_ctx *c, const mocd_params *p)
         c->ps.fint = reinterpret_cast<int64_t *>(q); q += sizeof(int64_t) * 2 * kMaxPop;
         c->ps.fval = reinterpret_cast<double *>(q); q += sizeof(double) * 2 * kMaxPop;
         c->ps.gen = reinterpret_cast<uint32_t *>(q);
+        c->ps.dcount = reinterpret_cast<int *>(q + 16);  // [2], within the 64-byte tail
         CK(cudaMemsetAsync(s, 0, bytes, c->stream));
         CK(cudaMemsetAsync(c->ps.q, 0, cells * sizeof(int32_t), c->stream));
         CK(cudaMemsetAsync(c->ps.buf[0], 0, cells * sizeof(int32_t), c->stream));
     }
     const size_t hist_need = (size_t)W * (size_t)c->n;
+    // The deferred-vote list holds every pair a generation can defer; its
+    // per-class counts are 32-bit.
+    if ((int64_t)p->pop_size * c->n_defer[0] > INT_MAX || (int64_t)p->pop_size * c->n_defer[1] > INT_MAX)
+        return MOCD_ERR_INVALID_ARG;
+    const size_t defer_need = (size_t)p->pop_size * (size_t)(c->n_defer[0] + c->n_defer[1]);
     {
         int rc = grow(c->stream, &c->ps.hist, &c->hist_cap, hist_need);
         if (rc) return rc;
+        if ((rc = grow(c->stream, &c->ps.hint, &c->hint_cap, (size_t)c->n))) return rc;
+        if ((rc = grow(c->stream, &c->ps.dlist, &c->dlist_cap, defer_need))) return rc;
     }
     c->W = W;
     c->params = *p;
@@ -265,11 +280,13 @@ int prepare_population(mocd_ctx *c, const mocd_params *p)
     gp.es = p->n_parents;
     gp.label_bits = label_bits_for(c->n);
     int hs = 0;
-    if (c->dmax > 32) {
-        hs = 128;
+    if (c->dmax > kDeferMax) {
+        hs = 256;
         while (hs < 2 * c->dmax) hs <<= 1;
     }
     gp.hash_size = hs;
+    gp.defer_cap[0] = (int)((int64_t)p->pop_size * c->n_defer[0]);
+    gp.defer_cap[1] = (int)((int64_t)p->pop_size * c->n_defer[1]);
     gp.m = c->m;
     gp.key0 = (uint32_t)p->seed;
     gp.key1 = (uint32_t)(p->seed >> 32);
@@ -278,6 +295,7 @@ int prepare_population(mocd_ctx *c, const mocd_params *p)
     c->occ_eval = grid_for_eval(c->sms);
     c->occ_eval_intra = grid_for_eval_intra(c->sms);
     c->occ_square = grid_for_square_sum(c->sms);
+    c->grid_vote = grid_for_vote(c->sms);
     c->occ_cross = grid_for_crossover(c->sms, gp.es);
     int smem = 0;
     c->occ_mut = grid_for_mutation(c->sms, gp.hash_size, &smem);
@@ -308,7 +326,7 @@ int issue_generation(mocd_ctx *c, cudaStream_t st, bool events)
     if (events) CK(mark(c, 0, st));
     CK(launch_crossover(gp, ps, c->grid_cross, st));
     if (events) CK(mark(c, 1, st));
-    CK(launch_mutation(gp, ps, c->d_row_ptr, c->d_col_idx, c->d_order, c->grid_mut, st));
+    CK(launch_mutation(gp, ps, c->d_row_ptr, c->d_col_idx, c->d_order, c->grid_mut, c->grid_vote, st));
     if (events) CK(mark(c, 2, st));
     CK(launch_evaluate_offspring(gp.n, gp.W, gp.np, c->d_row_ptr, c->d_col_idx, ps.q, ps.hist, ps.acc,
                                  c->grid_eval_intra, c->grid_square, st, c->d_order));
@@ -346,6 +364,8 @@ int start_population(mocd_ctx *c, uint32_t base_gen)
     int32_t *phalf = ps.buf[(base_gen + 1u) & 1u];
     int rc = clear_eval_state(c, ps.hist, (size_t)gp.W * (size_t)gp.n, ps.acc);
     if (rc) return rc;
+    // No mutation history yet: every node starts with the Misra-Gries pass.
+    CK(cudaMemsetAsync(ps.hint, 0, sizeof(uint32_t) * (size_t)gp.n, c->stream));
     CK(launch_evaluate(gp.n, gp.W, gp.np, c->d_row_ptr, c->d_col_idx, phalf, ps.hist, ps.acc,
                        c->grid_eval, c->stream));
     // Generations expect a zero histogram (the mutation kernel adds into it).
@@ -720,6 +740,11 @@ int mocd_graph_upload(mocd_ctx **out, int64_t n, const int64_t *row_ptr, const i
     c->n = n;
     c->m = nnz / 2;
     c->dmax = dmax;
+    for (int64_t v = 0; v < n; ++v) {
+        const int64_t d = row_ptr[v + 1] - row_ptr[v];
+        if (d > 32 && d <= 64) c->n_defer[0] += 1;
+        else if (d > 64 && d <= kDeferMax) c->n_defer[1] += 1;
+    }
     std::vector<int32_t> rp32(n + 1);
     for (int64_t v = 0; v <= n; ++v) rp32[v] = (int32_t)row_ptr[v];
     void *p = nullptr;

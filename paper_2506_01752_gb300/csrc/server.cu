@@ -53,10 +53,10 @@ struct Job {
 };
 
 // Device bytes a job holds while it runs (mocd_job_footprint).
-int64_t footprint(int64_t n, int64_t nnz, int32_t pop)
+int64_t footprint(int64_t n, const int64_t *row_ptr, int32_t pop)
 {
     int64_t b = 0;
-    mocd_job_footprint(n, nnz, pop, &b);
+    mocd_job_footprint(n, row_ptr, pop, &b);
     return b;
 }
 
@@ -254,16 +254,23 @@ void scheduler(mocd_server *s)
 
 extern "C" {
 
-int mocd_job_footprint(int64_t n, int64_t nnz, int32_t pop_size, int64_t *bytes)
+int mocd_job_footprint(int64_t n, const int64_t *row_ptr, int32_t pop_size, int64_t *bytes)
 {
-    if (!bytes || n < 1 || nnz < 0 || pop_size < 1 || pop_size > mocd::kMaxPop) return MOCD_ERR_INVALID_ARG;
+    if (!bytes || !row_ptr || n < 1 || pop_size < 1 || pop_size > mocd::kMaxPop) return MOCD_ERR_INVALID_ARG;
+    const int64_t nnz = row_ptr[n];
+    int64_t deferred_nodes = 0;  // degree 33 .. kDeferMax: deferred mutation votes
+    for (int64_t v = 0; v < n; ++v) {
+        const int64_t d = row_ptr[v + 1] - row_ptr[v];
+        deferred_nodes += (d > 32 && d <= mocd::kDeferMax) ? 1 : 0;
+    }
     const int64_t W = (pop_size + 3) & ~3;
     const int64_t labels = 4 * n * W * 4;         // P halves, Q, post-crossover children
     const int64_t hist = W * n * 4;               // degree histogram
+    const int64_t mutation = n * 4 + deferred_nodes * pop_size * 8;  // per-node hints, deferred votes
     const int64_t graph = (n + 1) * 4 + nnz * 4 + n * 4 + 4;  // CSR, node order, symmetry flag
     const int64_t front = (int64_t)pop_size * n * 4 + 2 * mocd::kMaxPop * 4;  // front download
     const int64_t fixed = (int64_t)1 << 20;       // small state, graph executable, events
-    *bytes = labels + hist + graph + front + fixed;
+    *bytes = labels + hist + mutation + graph + front + fixed;
     return MOCD_OK;
 }
 
@@ -312,7 +319,7 @@ int mocd_server_submit(mocd_server *s, int64_t n, const int64_t *row_ptr, const 
     if (row_ptr[n] > 0) j->col_idx.assign(col_idx, col_idx + row_ptr[n]);
     j->params = *params;
     j->generations = generations;
-    j->footprint = footprint(n, row_ptr[n], params->pop_size);
+    j->footprint = footprint(n, row_ptr, params->pop_size);
     j->work = (double)(n + row_ptr[n]) * (double)(generations + 1);
     std::lock_guard<std::mutex> lock(s->mu);
     j->id = s->next_id++;

@@ -124,6 +124,6 @@ def test_job_footprint_bounds_the_pool_peak(pop):
     finally:
         mocd.destroy(h)
     _, peak = mocd.debug_pool_usage()
-    fp = mocd.job_footprint(n, nnz, pop)
+    fp = mocd.job_footprint(rp, pop)
     assert 0 < peak - cur0 <= fp + 16 * (2 << 20), (peak - cur0, fp)
     assert peak - cur0 >= 0.8 * fp, (peak - cur0, fp)  # and the estimate is not loose

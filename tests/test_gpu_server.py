@@ -45,11 +45,16 @@ def _drain(srv, ids, max_running):
     raise AssertionError("server did not finish")
 
 
+TIGHT = "tight"  # a budget just above the largest job's footprint: about one job at a time
+
+
 @pytest.mark.parametrize("budget,max_running,background", [
-    (1 << 34, 8, None), (6 << 20, 8, None), (1 << 34, 1, None),
-    (1 << 34, 8, 0), (6 << 20, 4, 1)])
+    (1 << 34, 8, None), (TIGHT, 8, None), (1 << 34, 1, None),
+    (1 << 34, 8, 0), (TIGHT, 4, 1)])
 def test_server_results_equal_alone(budget, max_running, background):
     jobs = _jobs()
+    if budget == TIGHT:
+        budget = max(mocd.job_footprint(rp, kw.get("pop_size", 100)) for (rp, _), kw, _ in jobs) + (1 << 20)
     srv = mocd.Server(budget, max_running=max_running, depth=3)
     if background is not None:
         srv.start(admission_threads=2, policy=background)
