@@ -25,9 +25,11 @@
  *     f2 = S / (4 m^2), each computed as one IEEE double division. Dominance
  *     (Sec. 2.2) compares (k1, k2) exactly.
  *
- * Limits: 1 <= N_p <= 128, 1 <= E_S <= 16, n < 2^30, 2m < 2^31, and a
- * maximum node degree of 512 for generations (the mutation's per-warp count
- * table lives in shared memory); evaluation alone has no degree limit.
+ * Limits: 1 <= N_p <= 128, 1 <= E_S <= 16, n < 2^30, 2m < 2^31, and
+ * N_p x (number of nodes of degree 33..128 or above 512) < 2^31. There is no
+ * degree limit: the mutation's count tables of hubs above degree 512 live in
+ * a global scratch of at most 1 GiB per context (one table per warp of the
+ * hub kernel, each 2 x the smallest power of two >= 2 d_max ints).
  */
 #ifndef MOCD_H
 #define MOCD_H
@@ -95,8 +97,7 @@ int mocd_graph_upload(mocd_ctx **out, int64_t n, const int64_t *row_ptr,
  * Create and evaluate the initial population P^(0) (Alg. 1 phases 1-2:
  * InitializePopulation, then EvaluateIndividual for each member), rank it and
  * draw the tournament of generation 1. Resets the generation counter to 0.
- * Errors: INVALID_ARG (params out of the limits above, or a node of degree
- * above 512), OUT_OF_MEMORY, CUDA.
+ * Errors: INVALID_ARG (params out of the limits above), OUT_OF_MEMORY, CUDA.
  */
 int mocd_population_init(mocd_ctx *ctx, const mocd_params *params);
 
@@ -314,8 +315,10 @@ void mocd_batch_destroy(mocd_batch *b);
  *                       the four label buffers and the degree histogram
  *                       (5 x 4 n W bytes, W = N_p rounded up to a multiple of
  *                       4), the CSR and node order, the mutation's per-node
- *                       hints (4 n) and deferred-vote list (8 N_p per node of
- *                       degree 33..128), the individual-major buffer of the
+ *                       hints (4 n), deferred-vote list (8 N_p per node of
+ *                       degree 33..128 or above 512) and hub count tables
+ *                       (graphs with a degree above 512), the individual-major
+ *                       buffer of the
  *                       front download (4 n N_p) and 1 MiB of small state.
  *                       Errors: INVALID_ARG.
  */

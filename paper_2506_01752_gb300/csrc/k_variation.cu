@@ -162,7 +162,7 @@ crossover_kernel(GenParams gp, const int32_t *buf0, const int32_t *buf1, int32_t
                  int *__restrict__ dcount)
 {
     // The mutation kernel that follows appends deferred pairs from zero.
-    if (blockIdx.x == 0 && threadIdx.x < 2) dcount[threadIdx.x] = 0;
+    if (blockIdx.x == 0 && threadIdx.x < 3) dcount[threadIdx.x] = 0;
     extern __shared__ int smem[];
     const int W = gp.W, np = gp.np, E = gp.es;
     const int nq = W >> 2;
@@ -417,6 +417,18 @@ __device__ __forceinline__ void cp_async_wait_all()
 constexpr int kTileStride = 33;  // padded row of the per-warp label tile
 constexpr int kTileRows = 32;    // neighbours whose labels the tile keeps
 static_assert(kDeferMax == 4 * kTileRows, "deferred classes: degrees 33..64 and 65..128");
+
+// Start of deferred-vote class c in the list: the classes are stored one
+// after the other (written with selects: indexing the kernel parameter array
+// at run time would copy it to local memory).
+__device__ __forceinline__ int defer_offset(const GenParams &gp, int c)
+{
+    return c == 0 ? 0 : c == 1 ? gp.defer_cap[0] : gp.defer_cap[0] + gp.defer_cap[1];
+}
+__device__ __forceinline__ int defer_capacity(const GenParams &gp, int c)
+{
+    return c == 0 ? gp.defer_cap[0] : c == 1 ? gp.defer_cap[1] : gp.defer_cap[2];
+}
 constexpr int kMutBlock = 128;   // mutation threads per block (shared memory bound)
 
 // Batcher's odd-even merge sort of x[0, N) (N a power of two), ascending,
@@ -547,8 +559,9 @@ __device__ __forceinline__ bool lane_votes(const int *tile, int deg, bool mine, 
 }
 
 // Exact neighbour-majority of one pair of a node with degree > kDeferMax by
-// the whole warp: a per-warp open-addressing
-// count table in shared memory, sized to the node (the
+// the whole warp: a per-warp open-addressing count table (in shared memory,
+// or for the hubs above kSharedTableMax in global scratch), sized to the
+// node (the
 // smallest power of two with at least 2 deg slots), filled with one insert
 // per distinct label of each 32-neighbour chunk (__match_any_sync gives the
 // multiplicity). The labels reaching the largest count are then compacted
@@ -560,6 +573,8 @@ __device__ __forceinline__ int warp_mode_table(const GenParams &gp, const int32_
                                             const int *tile_col, int i, int *hkey, int *hcnt, uint32_t tie_u,
                                             unsigned &best_count)
 {
+    // tile_col: the staged labels of the first kTileRows neighbours, or NULL
+    // (all are gathered from `child`).
     const int lane = threadIdx.x & 31;
     const int W = gp.W;
     // 2 deg <= 2 dmax <= the per-warp capacity, so the table fits.
@@ -576,8 +591,8 @@ __device__ __forceinline__ int warp_mode_table(const GenParams &gp, const int32_
         const bool in = e0 + lane < deg;
         int x = (int)(0x80000000u | lane);
         if (in)
-            x = e0 + lane < kTileRows ? tile_col[(e0 + lane) * kTileStride]
-                                      : child[(size_t)__ldg(col_idx + beg + e0 + lane) * W + i];
+            x = (tile_col && e0 + lane < kTileRows) ? tile_col[(e0 + lane) * kTileStride]
+                                                    : child[(size_t)__ldg(col_idx + beg + e0 + lane) * W + i];
         // One insert per distinct label of the chunk, with its multiplicity.
         const unsigned peers = __match_any_sync(kFull, x);
         if (in && (peers & ((1u << lane) - 1u)) == 0) {
@@ -599,22 +614,43 @@ __device__ __forceinline__ int warp_mode_table(const GenParams &gp, const int32_
     for (int s = 0; s < per_lane; ++s) mx_l = max(mx_l, (unsigned)hcnt[lane + 32 * s]);
     const unsigned mx = __reduce_max_sync(kFull, mx_l);
     best_count = mx;
-    unsigned act = 0;
-    for (int s = 0; s < per_lane; ++s)
-        if ((unsigned)hcnt[lane + 32 * s] == mx) act |= 1u << s;
-    // Compact the tied labels into hcnt[0, t) (the counts are no longer needed).
-    const unsigned mine = (unsigned)__popc(act);
-    unsigned incl = mine;
+    // The tied labels: compacted into hcnt[0, t) when each lane has at most
+    // 32 slots (a bit mask per lane); in larger (hub) tables the keys of the
+    // slots below the top count are cleared instead, and the tied labels are
+    // the keys still set, scanned over the whole table.
+    int t;
+    const int *tied;
+    int span;
+    if (per_lane <= 32) {
+        unsigned act = 0;
+        for (int s = 0; s < per_lane; ++s)
+            if ((unsigned)hcnt[lane + 32 * s] == mx) act |= 1u << s;
+        // Compact the tied labels into hcnt[0, t) (the counts are no longer needed).
+        const unsigned mine = (unsigned)__popc(act);
+        unsigned incl = mine;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const unsigned y = __shfl_up_sync(kFull, incl, d);
-        if (lane >= d) incl += y;
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned y = __shfl_up_sync(kFull, incl, d);
+            if (lane >= d) incl += y;
+        }
+        t = (int)__shfl_sync(kFull, incl, 31);
+        int at = (int)(incl - mine);
+        __syncwarp();
+        for (int s = 0; s < per_lane; ++s)
+            if ((act >> s) & 1u) hcnt[at++] = hkey[lane + 32 * s];
+        tied = hcnt;
+        span = t;
+    } else {
+        unsigned mine = 0;
+        for (int s = 0; s < per_lane; ++s) {
+            const int e = lane + 32 * s;
+            if ((unsigned)hcnt[e] == mx) ++mine;
+            else hkey[e] = -1;
+        }
+        t = (int)__reduce_add_sync(kFull, mine);
+        tied = hkey;
+        span = HS;
     }
-    const int t = (int)__shfl_sync(kFull, incl, 31);
-    int at = (int)(incl - mine);
-    __syncwarp();
-    for (int s = 0; s < per_lane; ++s)
-        if ((act >> s) & 1u) hcnt[at++] = hkey[lane + 32 * s];
     __syncwarp();
     const unsigned kk = t > 1 ? pick_index(tie_u, (uint32_t)t) : 0u;
     int res;
@@ -627,9 +663,10 @@ __device__ __forceinline__ int warp_mode_table(const GenParams &gp, const int32_
         for (int b = gp.label_bits - 1; b >= 0; --b) {
             const unsigned above = ~((2u << b) - 1u);  // the bits above b
             unsigned c = 0;
-            for (int e = lane; e < t; e += 32) {
-                const unsigned key = (unsigned)hcnt[e];
-                c += ((key & above) == prefix && ((key >> b) & 1u) == 0u) ? 1u : 0u;
+            for (int e = lane; e < span; e += 32) {
+                const int key = tied[e];
+                if (key < 0) continue;  // a cleared slot of a hub table
+                c += (((unsigned)key & above) == prefix && (((unsigned)key >> b) & 1u) == 0u) ? 1u : 0u;
             }
             const unsigned cnt = __reduce_add_sync(kFull, c);
             if (rank >= cnt) {
@@ -644,8 +681,8 @@ __device__ __forceinline__ int warp_mode_table(const GenParams &gp, const int32_
         int last = -1;
         for (unsigned s = 0; s <= kk; ++s) {
             unsigned my = 0xffffffffu;
-            for (int e = lane; e < t; e += 32) {
-                const int key = hcnt[e];
+            for (int e = lane; e < span; e += 32) {
+                const int key = tied[e];
                 if (key > last) my = min(my, (unsigned)key);
             }
             last = (int)__reduce_min_sync(kFull, my);
@@ -729,7 +766,7 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
             // pass settles. hint = (pairs << 16) | such pairs; 0: no history.
             const uint32_t h = deg > kTileRows ? hint[v] : 0u;
             const bool use_mg = deg > kTileRows && (h == 0u || 2u * (h & 0xffffu) >= (h >> 16));
-            const bool deferred_class = deg > kTileRows && deg <= kDeferMax;
+            const bool deferred_class = (deg > kTileRows && deg <= kDeferMax) || deg > kSharedTableMax;
             int nsettle = 0;  // pairs of v with 4 (best count) > deg, settled here
             bool have_tw = false;
             uint4 tw = make_uint4(0, 0, 0, 0);
@@ -853,9 +890,10 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                 if (rest && deferred_class) {
                     // Degrees kTileRows + 1 .. kDeferMax: the exact vote of every
                     // remaining pair runs in mutation_vote_kernel, one pair per
-                    // thread with its labels sorted in registers. Its slot of
-                    // the row holds -1 until then.
-                    const int cls = deg <= 2 * kTileRows ? 0 : 1;
+                    // thread with its labels sorted in registers; hubs above
+                    // kSharedTableMax: in mutation_hub_kernel, a warp per pair.
+                    // The pair's slot of the row holds -1 until then.
+                    const int cls = deg > kDeferMax ? 2 : deg <= 2 * kTileRows ? 0 : 1;
                     int first = 0;
                     if (lane == 0) first = atomicAdd(dcount + cls, __popc(rest));
                     first = __shfl_sync(kFull, first, 0);
@@ -864,8 +902,7 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                         // The capacity is the class's nodes x N_p, every pair
                         // a generation can defer: the check only keeps a
                         // corrupted count in bounds.
-                        const int cap = cls ? gp.defer_cap[1] : gp.defer_cap[0];
-                        if (at_list < cap) dlist[(cls ? gp.defer_cap[0] : 0) + at_list] = make_int2(v, i);
+                        if (at_list < defer_capacity(gp, cls)) dlist[defer_offset(gp, cls) + at_list] = make_int2(v, i);
                         s_res[i] = -1;
                     }
                     rest = 0;
@@ -1001,8 +1038,8 @@ mutation_vote_kernel(GenParams gp, int cls, const int32_t *__restrict__ row_ptr,
     constexpr int NW = (N + 63) / 64;
     const uint32_t g = *gen_ptr;
     const int W = gp.W;
-    const int total = min(dcount[cls], cls ? gp.defer_cap[1] : gp.defer_cap[0]);
-    const int2 *list = dlist + (cls ? gp.defer_cap[0] : 0);
+    const int total = min(dcount[cls], defer_capacity(gp, cls));
+    const int2 *list = dlist + defer_offset(gp, cls);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         const int2 e = list[t];
         const int v = e.x, i = e.y;
@@ -1071,6 +1108,40 @@ mutation_vote_kernel(GenParams gp, int cls, const int32_t *__restrict__ row_ptr,
         q[(size_t)v * W + i] = res;
         atomicAdd(hist + (size_t)res * W + i, (unsigned)deg);
         if (4 * best > deg) atomicAdd(hint + v, 1u);
+    }
+}
+
+// The listed votes of hubs above kSharedTableMax: a warp per pair, its count
+// table in the warp's slice of the global scratch (2 gp.hub_hs ints). Writes
+// the label into Q, adds deg(v) to the histogram and counts the pair in v's
+// hint when its best count c has 4 c > deg.
+__global__ void __launch_bounds__(kMutBlock)
+mutation_hub_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
+                    const int32_t *__restrict__ child, int32_t *__restrict__ q, const uint32_t *__restrict__ gen_ptr,
+                    uint32_t *__restrict__ hist, uint32_t *__restrict__ hint, const int2 *__restrict__ dlist,
+                    const int *__restrict__ dcount, int *__restrict__ hub_table)
+{
+    const uint32_t g = *gen_ptr;
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    int *hkey = hub_table + (size_t)warp * 2 * gp.hub_hs;
+    int *hcnt = hkey + gp.hub_hs;
+    const int total = min(dcount[2], defer_capacity(gp, 2));
+    const int2 *list = dlist + defer_offset(gp, 2);
+    for (int t = warp; t < total; t += nwarps) {
+        const int2 e = list[t];
+        const int v = e.x, i = e.y;
+        const int beg = __ldg(row_ptr + v);
+        const int deg = __ldg(row_ptr + v + 1) - beg;
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)v, (uint32_t)(i >> 2), g, kStageMutTie), gp.key0, gp.key1);
+        unsigned mx = 0;
+        const int lab = warp_mode_table(gp, child, col_idx, beg, deg, nullptr, i, hkey, hcnt, word_of(r, i & 3), mx);
+        if (lane == 0) {
+            q[(size_t)v * gp.W + i] = lab;
+            atomicAdd(hist + (size_t)lab * gp.W + i, (unsigned)deg);
+            if (4 * (int)mx > deg) atomicAdd(hint + v, 1u);
+        }
     }
 }
 
@@ -1176,6 +1247,12 @@ cudaError_t launch_mutation(const GenParams &gp, const PopState &ps, const int32
     if (gp.defer_cap[1] > 0) {
         mutation_vote_kernel<kDeferMax><<<vote_grid, kMutBlock, 0, s>>>(gp, 1, row_ptr, col_idx, ps.c, ps.q, ps.gen,
                                                                         ps.hist, ps.hint, ps.dlist, ps.dcount);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (gp.defer_cap[2] > 0) {
+        mutation_hub_kernel<<<gp.hub_warps / (kMutBlock / 32), kMutBlock, 0, s>>>(
+            gp, row_ptr, col_idx, ps.c, ps.q, ps.gen, ps.hist, ps.hint, ps.dlist, ps.dcount, ps.hub_table);
         e = cudaGetLastError();
     }
     return e;

@@ -40,6 +40,10 @@ constexpr int kBlock = 256;       // threads per block of the node-parallel kern
 // pass leaves open run one pair per thread in a second kernel (degree
 // classes 33..64 and 65..128); higher degrees use a per-warp count table.
 constexpr int kDeferMax = 128;
+// Above this degree a node's count table no longer fits in shared memory:
+// its open pairs are listed for mutation_hub_kernel, which keeps the table of
+// each pair in a per-warp slice of global scratch.
+constexpr int kSharedTableMax = 512;
 
 // Random stream stages (third word of the Philox counter is the generation).
 constexpr uint32_t kStageInit = 1;
@@ -67,7 +71,8 @@ struct PopState {
     double *fval;             // [2][kMaxPop]: f1, f2 of each front member
     uint32_t *hint;           // [n]: (mutating pairs << 16) | pairs with a label above deg / 4, last generation
     int2 *dlist;              // deferred mutation votes (node, child): class 0 then class 1
-    int *dcount;              // [2]: deferred votes appended this generation, per class
+    int *dcount;              // [3]: deferred votes appended this generation: degree 33..64, 65..128, hubs
+    int *hub_table;           // hub_warps x 2 hub_hs: per-warp count tables of the hub votes
 };
 
 struct GenParams {
@@ -77,7 +82,9 @@ struct GenParams {
     int es;                   // E_S
     int label_bits;           // bits needed for a label in [0, n)
     int hash_size;            // per-warp hash entries for degree > kDeferMax (0: none)
-    int defer_cap[2];         // deferred-vote capacity per class: N_p x nodes of the class
+    int defer_cap[3];         // deferred-vote capacity per class: N_p x nodes of the class
+    int hub_hs;               // slots of a hub count table (power of two >= 2 dmax; 0: no hubs)
+    int hub_warps;            // warps of mutation_hub_kernel (one table slice each)
     int64_t m;                // edges
     uint32_t key0, key1;      // Philox key (seed)
     unsigned long long thr_c; // crossover iff u <= thr_c

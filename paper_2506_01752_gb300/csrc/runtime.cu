@@ -37,7 +37,7 @@ struct mocd_ctx {
 
     int64_t n = 0, m = 0;
     int dmax = 0;
-    int64_t n_defer[2] = {0, 0};  // nodes of degree 33..64 and 65..128 (deferred mutation votes)
+    int64_t n_defer[3] = {0, 0, 0};  // nodes of degree 33..64, 65..128 and > 512 (deferred mutation votes)
     int32_t *d_row_ptr = nullptr;
     int32_t *d_col_idx = nullptr;
     int32_t *d_order = nullptr;   // nodes by degree, descending
@@ -52,6 +52,7 @@ struct mocd_ctx {
     size_t hist_cap = 0;    // entries of ps.hist
     size_t hint_cap = 0;    // entries of ps.hint
     size_t dlist_cap = 0;   // entries of ps.dlist
+    size_t hub_cap = 0;     // entries of ps.hub_table
     void *d_small = nullptr;
     int grid_eval = 0, grid_cross = 0, grid_mut = 0;
     int grid_eval_intra = 0, grid_square = 0, grid_vote = 0;
@@ -150,6 +151,7 @@ void free_population(mocd_ctx *c)
     dev_free(c->ps.hist, c->stream);
     dev_free(c->ps.hint, c->stream);
     dev_free(c->ps.dlist, c->stream);
+    dev_free(c->ps.hub_table, c->stream);
     dev_free(c->d_small, c->stream);
     c->ps = PopState{};
     c->d_small = nullptr;
@@ -157,6 +159,7 @@ void free_population(mocd_ctx *c)
     c->hist_cap = 0;
     c->hint_cap = 0;
     c->dlist_cap = 0;
+    c->hub_cap = 0;
     c->ready = false;
 }
 
@@ -175,7 +178,6 @@ int check_params(const mocd_ctx *c, const mocd_params *p)
     if (!(p->p_crossover >= 0.0 && p->p_crossover <= 1.0)) return MOCD_ERR_INVALID_ARG;
     if (!(p->p_mutation >= 0.0 && p->p_mutation <= 1.0)) return MOCD_ERR_INVALID_ARG;
     if (p->init_mode != 0 && p->init_mode != 1) return MOCD_ERR_INVALID_ARG;
-    if (c->dmax > 512) return MOCD_ERR_INVALID_ARG;  // mutation count table limit
     return MOCD_OK;
 }
 
@@ -253,7 +255,7 @@ int prepare_population(mocd_ctx *c, const mocd_params *p)
         c->ps.fint = reinterpret_cast<int64_t *>(q); q += sizeof(int64_t) * 2 * kMaxPop;
         c->ps.fval = reinterpret_cast<double *>(q); q += sizeof(double) * 2 * kMaxPop;
         c->ps.gen = reinterpret_cast<uint32_t *>(q);
-        c->ps.dcount = reinterpret_cast<int *>(q + 16);  // [2], within the 64-byte tail
+        c->ps.dcount = reinterpret_cast<int *>(q + 16);  // [3], within the 64-byte tail
         CK(cudaMemsetAsync(s, 0, bytes, c->stream));
         CK(cudaMemsetAsync(c->ps.q, 0, cells * sizeof(int32_t), c->stream));
         CK(cudaMemsetAsync(c->ps.buf[0], 0, cells * sizeof(int32_t), c->stream));
@@ -261,14 +263,27 @@ int prepare_population(mocd_ctx *c, const mocd_params *p)
     const size_t hist_need = (size_t)W * (size_t)c->n;
     // The deferred-vote list holds every pair a generation can defer; its
     // per-class counts are 32-bit.
-    if ((int64_t)p->pop_size * c->n_defer[0] > INT_MAX || (int64_t)p->pop_size * c->n_defer[1] > INT_MAX)
+    if ((int64_t)p->pop_size * (c->n_defer[0] + c->n_defer[1] + c->n_defer[2]) > INT_MAX)
         return MOCD_ERR_INVALID_ARG;
-    const size_t defer_need = (size_t)p->pop_size * (size_t)(c->n_defer[0] + c->n_defer[1]);
+    const size_t defer_need = (size_t)p->pop_size * (size_t)(c->n_defer[0] + c->n_defer[1] + c->n_defer[2]);
+    // Hubs above the shared table's degree: one count table of hub_hs slots
+    // (keys and counts) per warp of the hub kernel, at most 1 GiB in all.
+    int hub_hs = 0, hub_warps = 0;
+    if (c->dmax > kSharedTableMax) {
+        hub_hs = 1024;
+        while (hub_hs < 2 * c->dmax) hub_hs <<= 1;
+        const int64_t per_warp = 2 * (int64_t)hub_hs * (int64_t)sizeof(int);
+        const int64_t fit = ((int64_t)1 << 30) / per_warp;
+        hub_warps = (int)std::max<int64_t>(4, std::min<int64_t>((int64_t)c->sms * 4, fit)) & ~3;
+    }
     {
         int rc = grow(c->stream, &c->ps.hist, &c->hist_cap, hist_need);
         if (rc) return rc;
         if ((rc = grow(c->stream, &c->ps.hint, &c->hint_cap, (size_t)c->n))) return rc;
         if ((rc = grow(c->stream, &c->ps.dlist, &c->dlist_cap, defer_need))) return rc;
+        if (hub_hs > 0 &&
+            (rc = grow(c->stream, &c->ps.hub_table, &c->hub_cap, (size_t)hub_warps * 2 * (size_t)hub_hs)))
+            return rc;
     }
     c->W = W;
     c->params = *p;
@@ -279,14 +294,17 @@ int prepare_population(mocd_ctx *c, const mocd_params *p)
     gp.np = p->pop_size;
     gp.es = p->n_parents;
     gp.label_bits = label_bits_for(c->n);
-    int hs = 0;
+    int hs = 0;  // shared count table of degrees kDeferMax + 1 .. kSharedTableMax
     if (c->dmax > kDeferMax) {
         hs = 256;
-        while (hs < 2 * c->dmax) hs <<= 1;
+        while (hs < 2 * std::min(c->dmax, kSharedTableMax)) hs <<= 1;
     }
     gp.hash_size = hs;
     gp.defer_cap[0] = (int)((int64_t)p->pop_size * c->n_defer[0]);
     gp.defer_cap[1] = (int)((int64_t)p->pop_size * c->n_defer[1]);
+    gp.defer_cap[2] = (int)((int64_t)p->pop_size * c->n_defer[2]);
+    gp.hub_hs = hub_hs;
+    gp.hub_warps = hub_warps;
     gp.m = c->m;
     gp.key0 = (uint32_t)p->seed;
     gp.key1 = (uint32_t)(p->seed >> 32);
@@ -744,6 +762,7 @@ int mocd_graph_upload(mocd_ctx **out, int64_t n, const int64_t *row_ptr, const i
         const int64_t d = row_ptr[v + 1] - row_ptr[v];
         if (d > 32 && d <= 64) c->n_defer[0] += 1;
         else if (d > 64 && d <= kDeferMax) c->n_defer[1] += 1;
+        else if (d > kSharedTableMax) c->n_defer[2] += 1;
     }
     std::vector<int32_t> rp32(n + 1);
     for (int64_t v = 0; v <= n; ++v) rp32[v] = (int32_t)row_ptr[v];

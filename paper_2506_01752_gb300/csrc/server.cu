@@ -258,15 +258,34 @@ int mocd_job_footprint(int64_t n, const int64_t *row_ptr, int32_t pop_size, int6
 {
     if (!bytes || !row_ptr || n < 1 || pop_size < 1 || pop_size > mocd::kMaxPop) return MOCD_ERR_INVALID_ARG;
     const int64_t nnz = row_ptr[n];
-    int64_t deferred_nodes = 0;  // degree 33 .. kDeferMax: deferred mutation votes
+    int64_t deferred_nodes = 0;  // degree 33 .. kDeferMax and hubs: deferred mutation votes
+    int64_t dmax = 0;
     for (int64_t v = 0; v < n; ++v) {
         const int64_t d = row_ptr[v + 1] - row_ptr[v];
-        deferred_nodes += (d > 32 && d <= mocd::kDeferMax) ? 1 : 0;
+        deferred_nodes += ((d > 32 && d <= mocd::kDeferMax) || d > mocd::kSharedTableMax) ? 1 : 0;
+        dmax = d > dmax ? d : dmax;
+    }
+    // The hub count tables: per warp of the hub kernel (at most four per SM),
+    // 2 x the smallest power of two >= max(1024, 2 dmax) ints, 1 GiB at most.
+    int64_t hub_tables = 0;
+    if (dmax > mocd::kSharedTableMax) {
+        int64_t hs = 1024;
+        while (hs < 2 * dmax) hs <<= 1;
+        int dev = 0, sms = 152;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            sms = 152;
+        }
+        const int64_t per_warp = 2 * hs * 4;
+        int64_t warps = ((int64_t)1 << 30) / per_warp;
+        if (warps > 4 * (int64_t)sms) warps = 4 * (int64_t)sms;
+        if (warps < 4) warps = 4;
+        hub_tables = (warps & ~3ll) * per_warp;
     }
     const int64_t W = (pop_size + 3) & ~3;
     const int64_t labels = 4 * n * W * 4;         // P halves, Q, post-crossover children
     const int64_t hist = W * n * 4;               // degree histogram
-    const int64_t mutation = n * 4 + deferred_nodes * pop_size * 8;  // per-node hints, deferred votes
+    const int64_t mutation = n * 4 + deferred_nodes * pop_size * 8 + hub_tables;  // hints, deferred votes
     const int64_t graph = (n + 1) * 4 + nnz * 4 + n * 4 + 4;  // CSR, node order, symmetry flag
     const int64_t front = (int64_t)pop_size * n * 4 + 2 * mocd::kMaxPop * 4;  // front download
     const int64_t fixed = (int64_t)1 << 20;       // small state, graph executable, events

@@ -204,7 +204,7 @@ def test_generations_match_oracle(gname, G, kw):
 
 
 @pytest.mark.parametrize("gname,G,kw", [
-    ("hub512", 3, dict(pop_size=24, p_mutation=1.0)),       # the largest degree the build takes
+    ("hub512", 3, dict(pop_size=24, p_mutation=1.0)),       # the largest degree of the shared count table
     ("hub512", 2, dict(pop_size=40, seed=(1 << 40) + 7)),
     ("one-edge", 3, dict(pop_size=20, p_mutation=1.0)),     # thousands of isolated nodes
     ("k40", 4, dict(pop_size=30, p_mutation=0.5)),          # one dense community, degree 39
@@ -258,16 +258,37 @@ def test_upload_rejects_asymmetric_graphs():
     assert e.value.status == -3
 
 
-def test_degree_above_the_limit_rejected():
-    """Degree 513 exceeds the mutation count table: the graph uploads (it is
-    valid) but a population on it is refused with INVALID_ARG."""
-    rp, ci = hub_of_degree(513)
+@pytest.mark.parametrize("gname,G,kw", [
+    ("hub2000", 3, dict(pop_size=24, p_mutation=1.0)),      # global count tables, every pair
+    ("hub2000", 3, dict(pop_size=64, seed=3)),
+    ("hub10000", 2, dict(pop_size=16, p_mutation=1.0)),
+    ("hub-ladder", 3, dict(pop_size=40, p_mutation=1.0)),   # 511, 512 (shared table), 513, 1024 (global)
+    ("lfr-hubs", 3, dict(pop_size=64, seed=2)),              # n = 100k, 263 nodes above 512, max 1709
+])
+def test_hub_degrees_match_oracle(gname, G, kw):
+    """Degrees above the shared count table (512): the open votes of these
+    hubs run in the hub kernel with count tables in global scratch; the
+    paper's mutation has no degree limit (Sec. 4.3.2). Whole generations
+    bit-exact against the oracle, and evaluation too."""
+    rp, ci = {
+        "hub2000": lambda: hub_of_degree(2000, extra=3000, seed=1),
+        "hub10000": lambda: hub_of_degree(10000, extra=12000, seed=2),
+        "hub-ladder": lambda: degree_ladder((1, 40, 100, 511, 512, 513, 1024)),
+        "lfr-hubs": lambda: synth.lfr_style(100_000, 20, 2000, 0.3, cmin=20, cmax=3000, seed=3)[:2],
+    }[gname]()
+    gp, op = _params(**kw)
+    m = int(rp[-1] // 2)
+    ref = oracle.population_init(rp, ci, op)
     with Ctx(rp, ci) as h:
-        with pytest.raises(mocd.MocdError) as e:
-            mocd.population_init(h, mocd.Params(pop_size=8))
-        assert e.value.status == -1
-        gi, gs = mocd.evaluate(h, synth.random_labels(rp.size - 1, 3, seed=1))
-        oi, os_ = oracle.objectives(rp, ci, synth.random_labels(rp.size - 1, 3, seed=1))
+        mocd.population_init(h, gp)
+        _compare_state(h, ref, m)
+        for step in range(G):
+            mocd.generation(h, 1)
+            ref = oracle.run_parallel(rp, ci, op, ref, 1)
+            _compare_state(h, ref, m)
+        lab = synth.random_labels(rp.size - 1, 3, seed=1)
+        gi, gs = mocd.evaluate(h, lab)
+        oi, os_ = oracle.objectives(rp, ci, lab)
         assert np.array_equal(gi, oi) and np.array_equal(gs, os_)
 
 
