@@ -7,6 +7,8 @@
 // stream counter of (child i, node v) is (v, i / 4, g, stage), word i % 4.
 #include <limits.h>
 
+#include <utility>
+
 #include "mocd_internal.h"
 #include "philox.cuh"
 
@@ -329,9 +331,10 @@ crossover_kernel(GenParams gp, const int32_t *buf0, const int32_t *buf1, int32_t
 // (the pick(u, t)-th smallest). A warp takes a node; its lanes take the
 // node's selected children, whose neighbour labels are staged into a
 // per-warp tile (a column per pair). Degree <= 32: when many pairs are
-// selected, each lane sorts its own pair's labels in registers with an
-// odd-even merge network of 8, 16 or 32 entries and reads the tied labels
-// off the runs, all pairs at once; when few are, the whole warp votes on two
+// selected, each lane sorts its own pair's labels in registers with a
+// merge-exchange network of 8, 12, .., 28 or 32 entries (the smallest that
+// holds the degree) and reads the tied labels off the runs, all pairs at
+// once; when few are, the whole warp votes on two
 // pairs at a time (one neighbour per lane grouped by __match_any_sync, the
 // pick(u, t)-th tied label by removing minima or, for deep ranks, by sorting
 // the tied labels across the warp). Degree > 32: when the node's history says
@@ -431,8 +434,11 @@ __device__ __forceinline__ int defer_capacity(const GenParams &gp, int c)
 }
 constexpr int kMutBlock = 128;   // mutation threads per block (shared memory bound)
 
-// Batcher's odd-even merge sort of x[0, N) (N a power of two), ascending,
-// written as compile-time recursion so that every index is a constant and
+// Sorting networks for any N: Batcher's merge exchange in the form of
+// Knuth, TAOCP vol. 3, Sec. 5.2.2, Algorithm M (for a power of two it is
+// Batcher's odd-even merge sort: 19, 63, 191, 543 comparators for 8, 16, 32,
+// 64 entries; 41, 97, 127, 161 for 12, 20, 24, 28). The comparator list is
+// generated at compile time and unrolled, so every index is a constant and
 // the array stays in registers.
 template <int A, int B>
 __device__ __forceinline__ void cmp_exchange(int *x)
@@ -443,51 +449,62 @@ __device__ __forceinline__ void cmp_exchange(int *x)
     x[B] = hi;
 }
 
-// Compare-exchanges (i, i + R) for i = I, I + 2R, ... while i + R < END.
-template <int I, int R, int END>
-struct CmpRun {
-    static __device__ __forceinline__ void run(int *x)
+template <int N>
+struct MergeExchange {
+    // Calls f(i, i + d) for every comparator in order (Algorithm M, steps
+    // M1..M5: p = 2^(t-1), 2^(t-2), ..., 1; for each p the passes d = p,
+    // q - p, ... with r = 0 then p).
+    template <class F>
+    static constexpr void each(F f)
     {
-        if constexpr (I + R < END) {
-            cmp_exchange<I, I + R>(x);
-            CmpRun<I + 2 * R, R, END>::run(x);
+        int t = 0;
+        while ((1 << t) < N) ++t;
+        for (int p = t > 0 ? 1 << (t - 1) : 0; p > 0; p >>= 1) {
+            int q = 1 << (t - 1), r = 0, d = p;
+            while (d > 0) {
+                for (int i = 0; i < N - d; ++i)
+                    if ((i & p) == r) f(i, i + d);
+                d = q - p;
+                q >>= 1;
+                r = p;
+            }
         }
     }
+    static constexpr int count()
+    {
+        int c = 0;
+        each([&](int, int) { ++c; });
+        return c;
+    }
+    static constexpr int C = count();
+    struct List {
+        int a[C > 0 ? C : 1];
+        int b[C > 0 ? C : 1];
+    };
+    static constexpr List make()
+    {
+        List l{};
+        int k = 0;
+        each([&](int i, int j) {
+            l.a[k] = i;
+            l.b[k] = j;
+            ++k;
+        });
+        return l;
+    }
+    static constexpr List P = make();
 };
 
-// Merge of the two sorted halves of x[LO, LO + N), elements R apart.
-template <int LO, int N, int R>
-struct OddEvenMerge {
-    static __device__ __forceinline__ void run(int *x)
-    {
-        if constexpr (2 * R < N) {
-            OddEvenMerge<LO, N, 2 * R>::run(x);
-            OddEvenMerge<LO + R, N, 2 * R>::run(x);
-            CmpRun<LO + R, R, LO + N>::run(x);
-        } else {
-            cmp_exchange<LO, LO + R>(x);
-        }
-    }
-};
-
-// Sort of x[LO, HI] (inclusive).
-template <int LO, int HI>
-struct OddEvenSort {
-    static __device__ __forceinline__ void run(int *x)
-    {
-        if constexpr (HI > LO) {
-            constexpr int MID = LO + (HI - LO) / 2;
-            OddEvenSort<LO, MID>::run(x);
-            OddEvenSort<MID + 1, HI>::run(x);
-            OddEvenMerge<LO, HI - LO + 1, 1>::run(x);
-        }
-    }
-};
+template <int N, std::size_t... K>
+__device__ __forceinline__ void apply_network(int (&x)[N], std::index_sequence<K...>)
+{
+    (cmp_exchange<MergeExchange<N>::P.a[K], MergeExchange<N>::P.b[K]>(x), ...);
+}
 
 template <int N>
 __device__ __forceinline__ void sort_network(int (&x)[N])
 {
-    OddEvenSort<0, N - 1>::run(x);
+    apply_network<N>(x, std::make_index_sequence<MergeExchange<N>::C>{});
 }
 
 // Exact neighbour-majority of one pair by its own lane: the pair's deg <= N
@@ -495,11 +512,8 @@ __device__ __forceinline__ void sort_network(int (&x)[N])
 // labels then form runs, the longest runs are the tied labels in ascending
 // order, and the pick(u, t)-th of them is the result.
 template <int N>
-__device__ __forceinline__ int lane_mode(const int *col, int deg, uint32_t u, int &best_count)
+__device__ __forceinline__ int lane_pick(int (&x)[N], int deg, uint32_t u)
 {
-    int x[N];
-#pragma unroll
-    for (int j = 0; j < N; ++j) x[j] = j < deg ? col[j * kTileStride] : INT_MAX;
     sort_network<N>(x);
     // One pass: the longest run length among the deg real entries and the
     // mask of the positions where a run of that length ends.
@@ -515,7 +529,6 @@ __device__ __forceinline__ int lane_mode(const int *col, int deg, uint32_t u, in
         }
         if (last && run == best) ends |= 1u << j;
     }
-    best_count = best;
     const int t = __popc(ends);
     const unsigned kk = t > 1 ? pick_index(u, (uint32_t)t) : 0u;
     // Position of the kk-th set bit of `ends`, halving the window each step.
@@ -539,12 +552,11 @@ __device__ __forceinline__ int lane_mode(const int *col, int deg, uint32_t u, in
     return res;
 }
 
-// Lane-parallel exact vote of every unresolved pair of a node with
-// deg <= kTileRows; unresolved lanes write their result. Returns, for the
-// lane's pair, whether its best count c has 4 c > deg (the pairs the
-// Misra-Gries pass would have settled).
+// Lane-parallel exact vote of every selected pair of a node with
+// deg <= kTileRows (N >= deg): each lane sorts its pair's deg labels (its
+// column of the staged tile) in registers and writes its result.
 template <int N>
-__device__ __forceinline__ bool lane_votes(const int *tile, int deg, bool mine, int i, uint4 tw, int *s_res)
+__device__ __forceinline__ void lane_votes(const int *tile, int deg, bool mine, int i, uint4 tw, int *s_res)
 {
     const int src = i >> 2;
     const uint32_t w0 = __shfl_sync(0xffffffffu, tw.x, src);
@@ -553,9 +565,19 @@ __device__ __forceinline__ bool lane_votes(const int *tile, int deg, bool mine, 
     const uint32_t w3 = __shfl_sync(0xffffffffu, tw.w, src);
     const int k = i & 3;
     const uint32_t u = k == 0 ? w0 : (k == 1 ? w1 : (k == 2 ? w2 : w3));
-    int best = 0;
-    if (mine) s_res[i] = lane_mode<N>(tile + (threadIdx.x & 31), deg, u, best);
-    return mine && 4 * best > deg;
+    const int *col = tile + (threadIdx.x & 31);
+    int x[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) x[j] = j < deg ? col[j * kTileStride] : INT_MAX;
+    const int res = lane_pick<N>(x, deg, u);
+    if (mine) s_res[i] = res;
+}
+
+// The smallest network size of the per-lane vote that holds deg labels, and
+// the fewest pairs (lanes) for which the per-lane vote beats the warp vote.
+__device__ __forceinline__ int lane_vote_min_pairs(int deg)
+{
+    return deg <= 8 ? 2 : deg <= 16 ? 5 : 10;
 }
 
 // Exact neighbour-majority of one pair of a node with degree > kDeferMax by
@@ -798,7 +820,10 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                 };
                 // The tile is read by the pass and by the votes of degree <= 32
                 // and > kDeferMax; pairs of the deferred degrees need it only
-                // for the pass.
+                // for the pass. Degree <= kTileRows with enough selected pairs
+                // takes the per-lane vote, else the warp vote.
+                const bool lane_path =
+                    deg <= kTileRows && __popc(__ballot_sync(kFull, has)) >= lane_vote_min_pairs(deg);
                 const int dt = (use_mg || !deferred_class) ? min(deg, kTileRows) : 0;
                 for (int j = 0; j < dt; ++j) {
                     const int u = __shfl_sync(kFull, my_u0, j);
@@ -911,23 +936,19 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                     tw = tie_words(gp, v, lane, g);
                     have_tw = true;
                 }
-                if (deg <= kTileRows) {
-                    // Many unresolved pairs: every lane settles its own pair
-                    // with a sorting network (all pairs at once).
-                    const int nrest = __popc(rest);
+                if (lane_path) {
+                    // Many selected pairs: every lane settles its own pair with
+                    // a sorting network of the smallest size that holds deg
+                    // labels (all pairs at once).
                     const bool mine = (rest >> lane) & 1u;
-                    bool settles = false;
-                    if (deg <= 8 && nrest >= 2) {
-                        settles = lane_votes<8>(tile, deg, mine, i, tw, s_res);
-                        rest = 0;
-                    } else if (deg > 8 && deg <= 16 && nrest >= 5) {
-                        settles = lane_votes<16>(tile, deg, mine, i, tw, s_res);
-                        rest = 0;
-                    } else if (deg > 16 && nrest >= 10) {
-                        settles = lane_votes<32>(tile, deg, mine, i, tw, s_res);
-                        rest = 0;
-                    }
-                    nsettle += __popc(__ballot_sync(kFull, settles));
+                    if (deg <= 8) lane_votes<8>(tile, deg, mine, i, tw, s_res);
+                    else if (deg <= 12) lane_votes<12>(tile, deg, mine, i, tw, s_res);
+                    else if (deg <= 16) lane_votes<16>(tile, deg, mine, i, tw, s_res);
+                    else if (deg <= 20) lane_votes<20>(tile, deg, mine, i, tw, s_res);
+                    else if (deg <= 24) lane_votes<24>(tile, deg, mine, i, tw, s_res);
+                    else if (deg <= 28) lane_votes<28>(tile, deg, mine, i, tw, s_res);
+                    else lane_votes<32>(tile, deg, mine, i, tw, s_res);
+                    rest = 0;
                 }
                 if (deg <= kTileRows) {
                     // Exact vote by the whole warp (lane = neighbour), two
@@ -979,7 +1000,6 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                             s_res[ia] = ra;
                             if (two) s_res[ib] = rb;
                         }
-                        nsettle += (4 * (int)ma > deg ? 1 : 0) + ((two && 4 * (int)mb > deg) ? 1 : 0);
                     }
                 }
                 // Degree > kDeferMax: a shared count table, one pair at a time.
