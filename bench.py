@@ -580,9 +580,11 @@ def run_batch(args):
     init_all()
     b = mocd.batch_create(ctxs, stream)
     shape = mocd.batch_autotune(b, 2)
+    _, merged = mocd.batch_form(b)
     mocd.batch_destroy(b)
     init_all()
     b = mocd.batch_create(ctxs, stream)
+    mocd.batch_configure(b, shape, merged)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
 
@@ -604,6 +606,16 @@ def run_batch(args):
     sampler = ClockSampler(_gpu_index())
     sampler.start()
     batch_ms = timed(lambda: mocd.batch_generation(b, 1))
+    mocd.batch_synchronize(b)
+    mocd.batch_destroy(b)
+    # The other selection form at the same shape, for comparison (the same
+    # generations of fresh populations).
+    init_all()
+    b = mocd.batch_create(ctxs, stream)
+    mocd.batch_configure(b, shape, not merged)
+    mocd.batch_generation(b, args.warmup)
+    mocd.batch_synchronize(b)
+    other_ms = timed(lambda: mocd.batch_generation(b, 1))
     mocd.batch_synchronize(b)
     mocd.batch_destroy(b)
 
@@ -643,6 +655,8 @@ def run_batch(args):
     line = {
         "metric": METRIC + " [batched jobs]", "value": units / (bt / 1e3), "unit": UNIT,
         "value_plain": units / (pt / 1e3), "speedup_vs_plain": pt / bt,
+        "selection_form": "merged (one launch for all members)" if merged else "per member",
+        "ms_per_step_other_form": statistics.fmean(other_ms),
         "ms_per_step": bt, "ms_per_step_plain": pt, "steps": args.steps, "warmup": args.warmup,
         "job_latency_ms": {"batched_p50": float(np.percentile(batch_lat, 50)),
                            "batched_p99": float(np.percentile(batch_lat, 99)),

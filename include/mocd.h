@@ -51,7 +51,8 @@ enum {
     MOCD_ERR_BUFFER_TOO_SMALL = -7,/* caller's capacity below the result size (count set) */
     MOCD_ERR_CUDA = -8,            /* a CUDA call failed */
     MOCD_ERR_NOT_READY = -9,       /* population not initialised yet */
-    MOCD_ERR_TOO_LARGE = -10       /* count * n exceeds MOCD_NOALLOC_MAX_CELLS */
+    MOCD_ERR_TOO_LARGE = -10,      /* count * n exceeds MOCD_NOALLOC_MAX_CELLS */
+    MOCD_ERR_CANCELLED = -11       /* the server job was cancelled */
 };
 
 /* Histogram cells (count * n) the fixed scratch of mocd_evaluate_noalloc holds. */
@@ -266,17 +267,29 @@ int mocd_evaluate_noalloc(const int32_t *row_ptr, const int32_t *col_idx, int64_
  *                       a member invalidates the batch (NOT_READY).
  *   mocd_batch_autotune picks the launch shape (nodes per warp of the node
  *                       kernels, one of 1, 2, 4, 8, 16) with the shortest
- *                       measured batch generation; each trial runs
+ *                       measured batch generation, then the selection form
+ *                       at that shape (below); each trial runs
  *                       `generations_per_trial` generations, so the
  *                       populations advance (re-initialise afterwards for a
  *                       run from generation 0). Results never depend on the
- *                       launch shape. Writes the choice to *nodes_per_warp.
+ *                       launch shape or form. Writes the shape to
+ *                       *nodes_per_warp.
+ *   mocd_batch_configure sets the form explicitly: the nodes per warp (1, 2,
+ *                       4, 8 or 16) and merged_select: 0 runs each member's
+ *                       environmental selection at the end of its own kernel
+ *                       chain (the chains proceed independently), 1 runs the
+ *                       selections of all members in one launch (a block per
+ *                       member) after every chain has evaluated.
+ *                       Errors: INVALID_ARG, NOT_READY, CUDA.
+ *   mocd_batch_form     reports the current nodes per warp and selection form.
  */
 typedef struct mocd_batch mocd_batch;
 int mocd_batch_create(mocd_batch **out, int32_t count, mocd_ctx *const *ctxs, void *cuda_stream);
 int mocd_batch_generation(mocd_batch *b, int32_t n_generations);
 int mocd_batch_autotune(mocd_batch *b, int32_t generations_per_trial, int32_t *nodes_per_warp);
 int mocd_batch_synchronize(mocd_batch *b);
+int mocd_batch_configure(mocd_batch *b, int32_t nodes_per_warp, int32_t merged_select);
+int mocd_batch_form(mocd_batch *b, int32_t *nodes_per_warp, int32_t *merged_select);
 void mocd_batch_destroy(mocd_batch *b);
 
 /*
@@ -299,15 +312,28 @@ void mocd_batch_destroy(mocd_batch *b);
  *   mocd_server_submit  copies the host CSR (validated at admission); the
  *                       job id is written to *job_id (ids start at 1).
  *   mocd_server_job_state  *state: 0 queued, 1 running, 2 done, 3 failed
- *                       (*status then holds the MOCD_ERR_* code).
- *   mocd_server_result  as mocd_pareto_front, for a done job.
+ *                       (*status then holds the MOCD_ERR_* code), 4 cancelled.
+ *   mocd_server_cancel  cancels a job: a queued job at once; an admitted job
+ *                       gets no further generations and is retired (its
+ *                       device memory released, its state cancelled) by a
+ *                       later round, once the generations already issued for
+ *                       it have completed. OK for a job already cancelled;
+ *                       INVALID_ARG for an unknown or finished job.
+ *   mocd_server_result  as mocd_pareto_front, for a done job; the job's
+ *                       status for a failed or cancelled one, NOT_READY
+ *                       while it is queued or running.
  *   mocd_server_start   switches to background mode: a scheduler thread runs
  *                       the rounds (mocd_server_step then only reports counts)
  *                       and `admission_threads` workers (1..16) validate,
  *                       upload and initialise admitted jobs while the GPU runs
  *                       the others. policy 0 admits in submission order;
- *                       policy 1 admits the queued job with the least work
- *                       ((n + 2m) x (G + 1)) first.
+ *                       policy 1 admits the queued job with the highest
+ *                       response ratio (waiting time + estimated run time) /
+ *                       estimated run time, the run time estimated from its
+ *                       size (n + 2m) x (G + 1) and the measured time per
+ *                       unit of size of the jobs completed so far: short jobs
+ *                       first, and a waiting job's priority grows until it is
+ *                       admitted.
  * Calls on one server may come from any host thread.
  *   mocd_job_footprint  the device bytes the server accounts for a job on the
  *                       graph with host row pointers row_ptr[n + 1] while it
@@ -329,6 +355,7 @@ int mocd_server_submit(mocd_server *s, int64_t n, const int64_t *row_ptr, const 
                        const mocd_params *params, int32_t generations, int64_t *job_id);
 int mocd_server_step(mocd_server *s, int32_t *running, int32_t *queued, int32_t *done);
 int mocd_server_job_state(mocd_server *s, int64_t job_id, int32_t *state, int32_t *status);
+int mocd_server_cancel(mocd_server *s, int64_t job_id);
 int mocd_server_result(mocd_server *s, int64_t job_id, int32_t cap, int32_t *count, int32_t *labels,
                        double *f1, double *f2, int64_t *intra, int64_t *sumsq, int32_t *best);
 void mocd_server_destroy(mocd_server *s);

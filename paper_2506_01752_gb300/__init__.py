@@ -23,6 +23,7 @@ __all__ = [
     "get_population", "get_offspring", "set_population", "evaluate", "synchronize",
     "set_timing", "kernel_times", "info", "destroy", "status_string", "evaluate_noalloc",
     "batch_create", "batch_generation", "batch_autotune", "batch_synchronize", "batch_destroy",
+    "batch_configure", "batch_form",
     "Server", "FrontStats", "front_stats", "select_solution", "job_footprint", "debug_inject",
     "debug_pool_usage", "SITE_DEVICE_ALLOC", "SITE_GENERATION",
     "SELECT_MODULARITY", "SELECT_COMMUNITIES", "SELECT_SIZE_VARIANCE", "SELECT_MEAN_CONDUCTANCE",
@@ -114,6 +115,8 @@ def load():
         "mocd_batch_autotune": (ctypes.c_int, [P, i32, P]),
         "mocd_batch_synchronize": (ctypes.c_int, [P]),
         "mocd_batch_destroy": (None, [P]),
+        "mocd_batch_configure": (ctypes.c_int, [P, i32, i32]),
+        "mocd_batch_form": (ctypes.c_int, [P, P, P]),
         "mocd_server_create": (ctypes.c_int, [ctypes.POINTER(P), i64, i32, i32]),
         "mocd_server_submit": (ctypes.c_int, [P, i64, P, P, ctypes.POINTER(_CParams), i32, P]),
         "mocd_server_start": (ctypes.c_int, [P, i32, i32]),
@@ -121,6 +124,7 @@ def load():
         "mocd_server_job_state": (ctypes.c_int, [P, i64, P, P]),
         "mocd_server_result": (ctypes.c_int, [P, i64, i32, P, P, P, P, P, P, P]),
         "mocd_server_destroy": (None, [P]),
+        "mocd_server_cancel": (ctypes.c_int, [P, i64]),
         "mocd_job_footprint": (ctypes.c_int, [i64, P, i32, P]),
         "mocd_debug_inject": (ctypes.c_int, [i32, i32, i32, i32]),
         "mocd_debug_pool_usage": (ctypes.c_int, [i32, P, P]),
@@ -307,6 +311,19 @@ def batch_autotune(b, generations_per_trial: int = 3) -> int:
     return out.value
 
 
+def batch_configure(b, nodes_per_warp: int = 1, merged_select: bool = False):
+    """Launch shape and selection form of a batch (see mocd_batch_configure)."""
+    _check(load().mocd_batch_configure(b, int(nodes_per_warp), 1 if merged_select else 0), "mocd_batch_configure")
+
+
+def batch_form(b):
+    """(nodes per warp, merged selection) of a batch."""
+    npw = ctypes.c_int32()
+    merged = ctypes.c_int32()
+    _check(load().mocd_batch_form(b, ctypes.byref(npw), ctypes.byref(merged)), "mocd_batch_form")
+    return npw.value, bool(merged.value)
+
+
 def batch_synchronize(b):
     _check(load().mocd_batch_synchronize(b), "mocd_batch_synchronize")
 
@@ -320,7 +337,7 @@ def batch_destroy(b):
 class Server:
     """Continuous-batching detection server (mocd_server_* in include/mocd.h)."""
 
-    QUEUED, RUNNING, DONE, FAILED = 0, 1, 2, 3
+    QUEUED, RUNNING, DONE, FAILED, CANCELLED = 0, 1, 2, 3, 4
 
     def __init__(self, hbm_budget_bytes: int, max_running: int = 64, depth: int = 2):
         self.h = ctypes.c_void_p()
@@ -350,6 +367,10 @@ class Server:
         d = ctypes.c_int32()
         _check(load().mocd_server_step(self.h, ctypes.byref(r), ctypes.byref(q), ctypes.byref(d)), "mocd_server_step")
         return r.value, q.value, d.value
+
+    def cancel(self, job_id: int):
+        """Cancel a queued or running job (retired by a later round)."""
+        _check(load().mocd_server_cancel(self.h, int(job_id)), "mocd_server_cancel")
 
     def state(self, job_id: int):
         st = ctypes.c_int32()

@@ -314,10 +314,11 @@ __device__ void rank_crowd_order(SelShared &S, int N, bool known_rank)
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kSelThreads)
-select_kernel(GenParams gp, PopState ps, int mode)
+// One block: selection of one population (mode 0: keys of a fresh P from
+// acc; mode 1: R = P u Q), then rank, crowding and order of P and the next
+// tournament.
+__device__ __forceinline__ void select_body(const GenParams &gp, const PopState &ps, int mode, SelShared &S)
 {
-    __shared__ SelShared S;
     const int p = threadIdx.x;  // loads, stores and the tournament: one thread per item
     const int np = gp.np;
     const long long m = gp.m;
@@ -406,6 +407,24 @@ select_kernel(GenParams gp, PopState ps, int mode)
     if (p == 0) *ps.gen = gn;
 }
 
+__global__ void __launch_bounds__(kSelThreads)
+select_kernel(GenParams gp, PopState ps, int mode)
+{
+    __shared__ SelShared S;
+    select_body(gp, ps, mode, S);
+}
+
+// The selections of several populations in one launch (a batch of
+// instances): block b selects population b.
+__global__ void __launch_bounds__(kSelThreads)
+select_multi_kernel(const GenParams *__restrict__ gps, const PopState *__restrict__ pss, int mode)
+{
+    __shared__ SelShared S;
+    const GenParams gp = gps[blockIdx.x];
+    const PopState ps = pss[blockIdx.x];
+    select_body(gp, ps, mode, S);
+}
+
 // F_1 of P in P order and SelectSolution: argmin of 4 m k1 + k2 (= argmax of
 // Q = 1 - f1 - f2), first member on ties. Also each member's exact intra and
 // S, and f1 = k1 / m, f2 = S / (4 m^2) as single IEEE divisions.
@@ -475,6 +494,12 @@ int blocks_for(int n)
 cudaError_t launch_select(const GenParams &gp, const PopState &ps, int mode, cudaStream_t s)
 {
     select_kernel<<<1, kSelThreads, 0, s>>>(gp, ps, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select_multi(const GenParams *gps, const PopState *pss, int count, int mode, cudaStream_t s)
+{
+    select_multi_kernel<<<count, kSelThreads, 0, s>>>(gps, pss, mode);
     return cudaGetLastError();
 }
 

@@ -111,6 +111,9 @@ cudaError_t launch_evaluate(int n, int W, int count, const int32_t *row_ptr, con
 // mode 0: keys of a fresh P from acc, keep = identity; mode 1: R = P u Q,
 // environmental selection. Both then rank P and draw the next tournament.
 cudaError_t launch_select(const GenParams &gp, const PopState &ps, int mode, cudaStream_t s);
+// The selections of `count` populations (device arrays of their parameters
+// and states) in one launch, a block each.
+cudaError_t launch_select_multi(const GenParams *gps, const PopState *pss, int count, int mode, cudaStream_t s);
 cudaError_t launch_front(const GenParams &gp, const PopState &ps, cudaStream_t s);
 // Community statistics of the `count` front members (front_kernel's list):
 // rows [n][round4(count)] ints, volsize [count][n] u64 and cut [count][n] u32

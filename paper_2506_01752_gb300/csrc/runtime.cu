@@ -337,7 +337,7 @@ cudaError_t mark(mocd_ctx *c, int k, cudaStream_t st)
 // One generation of Alg. 1 on stream st. The mutation kernel also clears the
 // accumulators and adds the offspring's degrees to the histogram that the
 // evaluation then squares (and zeroes).
-int issue_generation(mocd_ctx *c, cudaStream_t st, bool events)
+int issue_generation(mocd_ctx *c, cudaStream_t st, bool events, bool with_select = true)
 {
     const GenParams &gp = c->gp;
     const PopState &ps = c->ps;
@@ -349,6 +349,7 @@ int issue_generation(mocd_ctx *c, cudaStream_t st, bool events)
     CK(launch_evaluate_offspring(gp.n, gp.W, gp.np, c->d_row_ptr, c->d_col_idx, ps.q, ps.hist, ps.acc,
                                  c->grid_eval_intra, c->grid_square, st, c->d_order));
     if (events) CK(mark(c, 3, st));
+    if (!with_select) return MOCD_OK;  // a batch selects all its members in one launch
     CK(launch_select(gp, ps, 1, st));
     if (events) CK(mark(c, 4, st));
     return MOCD_OK;
@@ -676,6 +677,7 @@ const char *mocd_status_string(int status)
     case MOCD_ERR_CUDA: return "CUDA error";
     case MOCD_ERR_NOT_READY: return "population not initialised";
     case MOCD_ERR_TOO_LARGE: return "count * n exceeds the fixed scratch of the no-allocation entry point";
+    case MOCD_ERR_CANCELLED: return "job cancelled";
     default: return "unknown status";
     }
 }
@@ -1060,6 +1062,11 @@ struct mocd_batch {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // Selection of every member in one multi-population launch after the
+    // members' kernel chains, instead of one selection at the end of each.
+    bool merged_select = false;
+    GenParams *d_gp = nullptr;  // [count], for the merged selection
+    PopState *d_ps = nullptr;
     std::vector<mocd_ctx *> ctx;
     std::vector<int32_t> version;
     std::vector<cudaStream_t> branch;
@@ -1075,15 +1082,29 @@ static int batch_build(mocd_batch *b)
     if (b->graph) cudaGraphDestroy(b->graph);
     b->exec = nullptr;
     b->graph = nullptr;
+    if (b->merged_select) {
+        // The members' current parameters and states, for the merged selection.
+        std::vector<GenParams> gps;
+        std::vector<PopState> pss;
+        for (mocd_ctx *c : b->ctx) {
+            gps.push_back(c->gp);
+            pss.push_back(c->ps);
+        }
+        CK(cudaMemcpyAsync(b->d_gp, gps.data(), sizeof(GenParams) * gps.size(), cudaMemcpyHostToDevice, b->stream));
+        CK(cudaMemcpyAsync(b->d_ps, pss.data(), sizeof(PopState) * pss.size(), cudaMemcpyHostToDevice, b->stream));
+        CK(cudaStreamSynchronize(b->stream));
+    }
     CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     int rc = MOCD_OK;
     cudaError_t e = cudaEventRecord(b->fork, b->stream);
     for (size_t i = 0; i < b->ctx.size() && rc == MOCD_OK && e == cudaSuccess; ++i) {
         e = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
-        if (e == cudaSuccess) rc = issue_generation(b->ctx[i], b->branch[i], false);
+        if (e == cudaSuccess) rc = issue_generation(b->ctx[i], b->branch[i], false, !b->merged_select);
         if (rc == MOCD_OK && e == cudaSuccess) e = cudaEventRecord(b->join[i], b->branch[i]);
         if (rc == MOCD_OK && e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join[i], 0);
     }
+    if (rc == MOCD_OK && e == cudaSuccess && b->merged_select)
+        e = launch_select_multi(b->d_gp, b->d_ps, (int)b->ctx.size(), 1, b->stream);
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (rc || e != cudaSuccess || e2 != cudaSuccess) {
@@ -1123,6 +1144,13 @@ int mocd_batch_create(mocd_batch **out, int32_t count, mocd_ctx *const *ctxs, vo
         b->own_stream = true;
     }
     if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return fail(MOCD_ERR_CUDA);
+    {
+        void *p = nullptr;
+        if (dev_alloc(&p, sizeof(GenParams) * (size_t)count, b->stream) != cudaSuccess) return fail(MOCD_ERR_OUT_OF_MEMORY);
+        b->d_gp = static_cast<GenParams *>(p);
+        if (dev_alloc(&p, sizeof(PopState) * (size_t)count, b->stream) != cudaSuccess) return fail(MOCD_ERR_OUT_OF_MEMORY);
+        b->d_ps = static_cast<PopState *>(p);
+    }
     for (int32_t i = 0; i < count; ++i) {
         // Work already issued on a member's own stream finishes first.
         if (cudaStreamSynchronize(ctxs[i]->stream) != cudaSuccess) return fail(MOCD_ERR_CUDA);
@@ -1165,6 +1193,7 @@ int mocd_batch_autotune(mocd_batch *b, int32_t generations_per_trial, int32_t *n
 {
     if (!b || generations_per_trial < 1) return MOCD_ERR_INVALID_ARG;
     static const int kShapes[] = {1, 2, 4, 8, 16};
+    b->merged_select = false;  // the shapes are compared in the per-member form
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     CK(cudaEventCreate(&t0));
     CK(cudaEventCreate(&t1));
@@ -1191,18 +1220,58 @@ int mocd_batch_autotune(mocd_batch *b, int32_t generations_per_trial, int32_t *n
             best = shape;
         }
     }
+    // Then the selection form at that shape: per member, or merged.
+    bool best_merged = false;
+    if (rc == MOCD_OK) {
+        for (mocd_ctx *c : b->ctx) {
+            c->nodes_per_warp = best;
+            size_grids(c);
+        }
+        b->merged_select = true;
+        float ms = 0.0f;
+        if ((rc = batch_build(b)) == MOCD_OK && (rc = mocd_batch_generation(b, 1)) == MOCD_OK) {
+            if (cudaEventRecord(t0, b->stream) != cudaSuccess) rc = MOCD_ERR_CUDA;
+            if (rc == MOCD_OK) rc = mocd_batch_generation(b, generations_per_trial);
+            if (rc == MOCD_OK &&
+                (cudaEventRecord(t1, b->stream) != cudaSuccess || cudaEventSynchronize(t1) != cudaSuccess))
+                rc = MOCD_ERR_CUDA;
+            if (rc == MOCD_OK) cudaEventElapsedTime(&ms, t0, t1);
+            best_merged = rc == MOCD_OK && ms < best_ms;
+        }
+        b->merged_select = best_merged;
+    }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     if (rc) return rc;
+    if ((rc = mocd_batch_configure(b, best, best_merged ? 1 : 0))) return rc;
+    if (nodes_per_warp) *nodes_per_warp = best;
+    return MOCD_OK;
+}
+
+int mocd_batch_configure(mocd_batch *b, int32_t nodes_per_warp, int32_t merged_select)
+{
+    if (!b || (nodes_per_warp != 1 && nodes_per_warp != 2 && nodes_per_warp != 4 && nodes_per_warp != 8 &&
+               nodes_per_warp != 16))
+        return MOCD_ERR_INVALID_ARG;
+    for (size_t i = 0; i < b->ctx.size(); ++i)
+        if (!b->ctx[i]->ready || b->ctx[i]->version != b->version[i]) return MOCD_ERR_NOT_READY;
+    int rc;
     for (mocd_ctx *c : b->ctx) {
-        c->nodes_per_warp = best;
+        c->nodes_per_warp = nodes_per_warp;
         size_grids(c);
         // Keep each member's own generation graph in the same launch shape.
         drop_graphs(c);
         if ((rc = build_graph(c))) return rc;
     }
-    if ((rc = batch_build(b))) return rc;
-    if (nodes_per_warp) *nodes_per_warp = best;
+    b->merged_select = merged_select != 0;
+    return batch_build(b);
+}
+
+int mocd_batch_form(mocd_batch *b, int32_t *nodes_per_warp, int32_t *merged_select)
+{
+    if (!b || b->ctx.empty()) return MOCD_ERR_INVALID_ARG;
+    if (nodes_per_warp) *nodes_per_warp = b->ctx[0]->nodes_per_warp;
+    if (merged_select) *merged_select = b->merged_select ? 1 : 0;
     return MOCD_OK;
 }
 
@@ -1213,6 +1282,9 @@ void mocd_batch_destroy(mocd_batch *b)
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    dev_free(b->d_gp, b->stream);
+    dev_free(b->d_ps, b->stream);
+    if (b->stream) cudaStreamSynchronize(b->stream);
     for (cudaStream_t st : b->branch) cudaStreamDestroy(st);
     for (cudaEvent_t ev : b->join) cudaEventDestroy(ev);
     if (b->fork) cudaEventDestroy(b->fork);

@@ -12,6 +12,7 @@
 // is busy with the running ones.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -27,7 +28,9 @@
 
 namespace {
 
-enum { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3 };
+enum { kQueued = 0, kRunning = 1, kDone = 2, kFailed = 3, kCancelled = 4 };
+
+using Clock = std::chrono::steady_clock;
 
 struct Job {
     int64_t id = 0;
@@ -41,8 +44,11 @@ struct Job {
     int32_t generations = 0;
     int32_t issued = 0;
     int issue_error = MOCD_OK;  // first failure while issuing generations
+    bool cancel = false;        // cancellation requested while admitted
+    bool cancel_marked = false; // a marker after its last issued generation is recorded
+    Clock::time_point submitted, started;
     int64_t footprint = 0;
-    double work = 0.0;  // relative cost, for shortest-first admission
+    double work = 0.0;  // (n + 2m) x (G + 1): the admission policy's size of the job
     mocd_ctx *ctx = nullptr;
     cudaEvent_t done = nullptr;
     // result
@@ -67,7 +73,8 @@ struct mocd_server {
     int64_t used = 0;  // footprint of admitting and running jobs
     int32_t max_running = 1;
     int32_t depth = 1;
-    int32_t policy = 0;  // 0: first come first served, 1: smallest work first
+    int32_t policy = 0;  // 0: first come first served, 1: highest response ratio next
+    double sec_per_work = 3e-10;  // measured run time per unit of work (moving average)
     int64_t next_id = 1;
     int32_t done_count = 0;
     int device = 0;
@@ -114,14 +121,27 @@ int admit_job(Job *j)
     return rc;
 }
 
-// Next queued job to admit under the policy (front of the queue, or the
-// smallest piece of work).
+// Next queued job to admit under the policy: the front of the queue, or the
+// highest response ratio (waiting time + estimated run time) / estimated run
+// time, the run time estimated from the job's size and the measured time per
+// unit of work of the jobs completed so far. Short jobs go first, and a
+// waiting job's ratio grows until it is admitted, so no job starves.
 std::deque<Job *>::iterator pick(mocd_server *s)
 {
     auto it = s->queue.begin();
-    if (s->policy == 1)
-        for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
-            if ((*q)->work < (*it)->work) it = q;
+    if (s->policy == 1) {
+        const Clock::time_point now = Clock::now();
+        double best = -1.0;
+        for (auto q = s->queue.begin(); q != s->queue.end(); ++q) {
+            const double service = std::max((*q)->work * s->sec_per_work, 1e-6);
+            const double wait = std::chrono::duration<double>(now - (*q)->submitted).count();
+            const double ratio = (wait + service) / service;
+            if (ratio > best) {
+                best = ratio;
+                it = q;
+            }
+        }
+    }
     return it;
 }
 
@@ -129,9 +149,16 @@ std::deque<Job *>::iterator pick(mocd_server *s)
 // admitted jobs are handed to the workers instead of being initialised here.
 void round_locked(mocd_server *s, std::unique_lock<std::mutex> &lock)
 {
-    // 1. Retire jobs whose last generation has completed.
+    // 1. Retire jobs whose last generation has completed, and cancelled jobs
+    // once the generations already issued for them have completed.
     for (size_t k = 0; k < s->running.size();) {
         Job *j = s->running[k];
+        if (!j->admitting && j->cancel && !j->cancel_marked) {
+            // Nothing more is issued; the marker follows the work in flight.
+            if (mocd::record_on_stream(j->ctx, j->done) != MOCD_OK) j->issue_error = MOCD_ERR_CUDA;
+            j->cancel_marked = true;
+            j->issued = j->generations;
+        }
         if (j->admitting || j->issued < j->generations) {
             ++k;
             continue;
@@ -151,6 +178,8 @@ void round_locked(mocd_server *s, std::unique_lock<std::mutex> &lock)
         }
         if (q != cudaSuccess) {
             finish(s, j, kFailed, MOCD_ERR_CUDA);
+        } else if (j->cancel) {
+            finish(s, j, kCancelled, MOCD_ERR_CANCELLED);
         } else {
             const int64_t cap = j->params.pop_size;
             j->labels.resize((size_t)cap * (size_t)j->n);
@@ -161,6 +190,10 @@ void round_locked(mocd_server *s, std::unique_lock<std::mutex> &lock)
             const int rc = mocd_pareto_front(j->ctx, (int32_t)cap, &j->count, j->labels.data(), j->f1.data(),
                                              j->f2.data(), j->intra.data(), j->sumsq.data(), &j->best);
             if (rc == MOCD_OK) j->labels.resize((size_t)j->count * (size_t)j->n);
+            if (rc == MOCD_OK && j->work > 0.0) {
+                const double took = std::chrono::duration<double>(Clock::now() - j->started).count();
+                s->sec_per_work = 0.8 * s->sec_per_work + 0.2 * (took / j->work);
+            }
             finish(s, j, rc == MOCD_OK ? kDone : kFailed, rc);
         }
         s->running.erase(s->running.begin() + k);
@@ -180,6 +213,7 @@ void round_locked(mocd_server *s, std::unique_lock<std::mutex> &lock)
         s->queue.erase(it);
         s->used += j->footprint;
         j->admitting = true;
+        j->started = Clock::now();
         s->running.push_back(j);
         if (s->background) {
             s->to_admit.push_back(j);
@@ -200,7 +234,7 @@ void round_locked(mocd_server *s, std::unique_lock<std::mutex> &lock)
     }
     // 3. Enqueue more generations of every running job on its own stream.
     for (Job *j : s->running) {
-        if (j->admitting) continue;
+        if (j->admitting || j->cancel) continue;
         const int32_t k = j->generations - j->issued < s->depth ? j->generations - j->issued : s->depth;
         if (k <= 0) continue;
         int rc = mocd_generation(j->ctx, k);
@@ -340,6 +374,7 @@ int mocd_server_submit(mocd_server *s, int64_t n, const int64_t *row_ptr, const 
     j->generations = generations;
     j->footprint = footprint(n, row_ptr, params->pop_size);
     j->work = (double)(n + row_ptr[n]) * (double)(generations + 1);
+    j->submitted = Clock::now();
     std::lock_guard<std::mutex> lock(s->mu);
     j->id = s->next_id++;
     s->queue.push_back(j);
@@ -356,6 +391,30 @@ int mocd_server_step(mocd_server *s, int32_t *running, int32_t *queued, int32_t 
     if (running) *running = (int32_t)s->running.size();
     if (queued) *queued = (int32_t)s->queue.size();
     if (done) *done = s->done_count;
+    return MOCD_OK;
+}
+
+int mocd_server_cancel(mocd_server *s, int64_t job_id)
+{
+    if (!s) return MOCD_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->jobs.find(job_id);
+    if (it == s->jobs.end()) return MOCD_ERR_INVALID_ARG;
+    Job *j = it->second;
+    if (j->state == kCancelled) return MOCD_OK;
+    if (j->state == kDone || j->state == kFailed) return MOCD_ERR_INVALID_ARG;
+    for (auto q = s->queue.begin(); q != s->queue.end(); ++q) {
+        if (*q == j) {
+            s->queue.erase(q);
+            j->state = kCancelled;
+            j->status = MOCD_ERR_CANCELLED;
+            std::vector<int64_t>().swap(j->row_ptr);
+            std::vector<int32_t>().swap(j->col_idx);
+            s->done_count += 1;
+            return MOCD_OK;
+        }
+    }
+    j->cancel = true;  // admitted: retired by a later round
     return MOCD_OK;
 }
 
@@ -378,7 +437,7 @@ int mocd_server_result(mocd_server *s, int64_t job_id, int32_t cap, int32_t *cou
     auto it = s->jobs.find(job_id);
     if (it == s->jobs.end()) return MOCD_ERR_INVALID_ARG;
     Job *j = it->second;
-    if (j->state == kFailed) return j->status;
+    if (j->state == kFailed || j->state == kCancelled) return j->status;
     if (j->state != kDone) return MOCD_ERR_NOT_READY;
     *count = j->count;
     if (j->count > cap) return MOCD_ERR_BUFFER_TOO_SMALL;

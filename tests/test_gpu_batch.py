@@ -22,7 +22,7 @@ def _instances():
     ]
 
 
-def _run(autotune):
+def _run(autotune, merged=None):
     inst = _instances()
     ctxs = [mocd.graph_upload(rp, ci) for (rp, ci), _ in inst]
     try:
@@ -42,6 +42,9 @@ def _run(autotune):
                 assert e.value.status == -9
                 mocd.batch_destroy(b)
                 b = mocd.batch_create(ctxs)
+            if merged is not None:
+                mocd.batch_configure(b, 2, merged)
+                assert mocd.batch_form(b) == (2, merged)
             mocd.batch_generation(b, 4)
             mocd.batch_synchronize(b)
             for c, ((rp, ci), kw) in zip(ctxs, inst):
@@ -70,6 +73,13 @@ def test_batch_matches_oracle():
 
 def test_batch_after_autotune_matches_oracle():
     _run(autotune=True)
+
+
+@pytest.mark.parametrize("merged", [False, True])
+def test_batch_selection_forms_match_oracle(merged):
+    """The per-member selections and the one merged multi-population
+    selection launch give the same generations (the oracle's)."""
+    _run(autotune=False, merged=merged)
 
 
 def test_batch_rejects_bad_members():

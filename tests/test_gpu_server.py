@@ -103,3 +103,73 @@ def test_server_failures():
         assert e.value.status == -6
     finally:
         srv.close()
+
+
+@pytest.mark.parametrize("background", [False, True])
+def test_server_cancel_queued_and_running(background):
+    """A queued job cancelled at once; a running job cancelled between rounds
+    gets no further generations and is retired with its device memory
+    returned to the pool; the other jobs' results equal the same jobs alone."""
+    import time
+    jobs = _jobs()
+    base, _ = mocd.debug_pool_usage()
+    srv = mocd.Server(1 << 34, max_running=1, depth=2)
+    if background:
+        srv.start(admission_threads=1, policy=0)
+    try:
+        big = synth.lfr_style(20000, 16, 50, 0.3, seed=9)[:2]
+        j_run = srv.submit(big[0], big[1], mocd.Params(seed=1), 5000)   # long enough to be running
+        ids = [srv.submit(rp, ci, mocd.Params(**kw), G) for (rp, ci), kw, G in jobs]
+        j_queued = ids[1]
+        srv.cancel(j_queued)
+        assert srv.state(j_queued) == (mocd.Server.CANCELLED, -11)
+        t_end = time.time() + 60
+        while srv.state(j_run)[0] != mocd.Server.RUNNING:
+            assert time.time() < t_end
+            srv.step()
+            time.sleep(0.001)
+        for _ in range(5):
+            srv.step()
+        srv.cancel(j_run)
+        srv.cancel(j_run)  # cancelling again is harmless
+        _drain(srv, [j_run] + ids, 1)
+        assert srv.state(j_run) == (mocd.Server.CANCELLED, -11)
+        with pytest.raises(mocd.MocdError) as e:
+            srv.result(j_run)
+        assert e.value.status == -11
+        with pytest.raises(mocd.MocdError) as e:
+            srv.cancel(ids[0])  # finished jobs cannot be cancelled
+        assert e.value.status == -1
+        for k, (jid, ((rp, ci), kw, G)) in enumerate(zip(ids, jobs)):
+            if jid == j_queued:
+                continue
+            assert srv.state(jid) == (mocd.Server.DONE, 0)
+            got, ref = srv.result(jid), _alone(rp, ci, kw, G)
+            assert got.best == ref.best and np.array_equal(got.labels, ref.labels)
+    finally:
+        srv.close()
+    cur, _ = mocd.debug_pool_usage()
+    assert cur == base  # every job's device memory went back
+
+
+def test_server_response_ratio_admission_completes_everything():
+    """Admission by highest response ratio (policy 1) with one job at a time:
+    small jobs overtake a large one, every job finishes with its result equal
+    to the job run alone."""
+    jobs = _jobs()
+    big = synth.lfr_style(20000, 16, 50, 0.3, seed=9)[:2]
+    srv = mocd.Server(1 << 34, max_running=1, depth=4)
+    srv.start(admission_threads=1, policy=1)
+    try:
+        j_big = srv.submit(big[0], big[1], mocd.Params(seed=2), 30)
+        ids = [srv.submit(rp, ci, mocd.Params(**kw), G) for (rp, ci), kw, G in jobs]
+        _drain(srv, [j_big] + ids, 1)
+        for jid, ((rp, ci), kw, G) in zip(ids, jobs):
+            assert srv.state(jid) == (mocd.Server.DONE, 0)
+            got, ref = srv.result(jid), _alone(rp, ci, kw, G)
+            assert got.best == ref.best and np.array_equal(got.labels, ref.labels)
+        assert srv.state(j_big) == (mocd.Server.DONE, 0)
+        got, ref = srv.result(j_big), _alone(big[0], big[1], dict(seed=2), 30)
+        assert np.array_equal(got.labels, ref.labels)
+    finally:
+        srv.close()
