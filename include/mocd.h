@@ -379,6 +379,21 @@ enum { MOCD_SITE_DEVICE_ALLOC = 0, MOCD_SITE_GENERATION = 1 };
 int mocd_debug_inject(int32_t site, int32_t skip, int32_t count, int32_t status);
 
 /*
+ * Test support: the bounds checks of the debug build (the library built with
+ * -DMOCD_DEBUG_CHECKS, see paper_2506_01752_gb300.build.build(debug=True)).
+ * There the kernels check the invariants their memory accesses rely on (CSR
+ * row pointers non-decreasing, neighbour ids and labels in [0, n), indices
+ * into P u Q below 2 N_p); a failed check never traps: the access is skipped
+ * (or redirected in bounds) and the failure recorded. out[0] receives the
+ * number of failures since the last reset, out[1] the first failure's code
+ * (1 row pointers, 2 node id, 3 label, 4 index into P u Q) and out[2] its
+ * node or slot; reset != 0 then clears the record. Returns 1 in the debug
+ * build, 0 in the normal one (whose kernels check nothing: out is zero), or
+ * a negative status (INVALID_ARG, CUDA).
+ */
+int mocd_debug_checks(uint64_t *out, int32_t reset);
+
+/*
  * Test support: bytes in use now and the high-water mark since the last
  * reset in the current device's default stream-ordered memory pool, from
  * which every device allocation of the library comes (reset_peak != 0 first

@@ -25,7 +25,7 @@ __all__ = [
     "batch_create", "batch_generation", "batch_autotune", "batch_synchronize", "batch_destroy",
     "batch_configure", "batch_form",
     "Server", "FrontStats", "front_stats", "select_solution", "job_footprint", "debug_inject",
-    "debug_pool_usage", "SITE_DEVICE_ALLOC", "SITE_GENERATION",
+    "debug_pool_usage", "debug_checks", "load_library", "use_library", "SITE_DEVICE_ALLOC", "SITE_GENERATION",
     "SELECT_MODULARITY", "SELECT_COMMUNITIES", "SELECT_SIZE_VARIANCE", "SELECT_MEAN_CONDUCTANCE",
     "SELECT_MAX_CONDUCTANCE", "STAGES",
 ]
@@ -86,7 +86,14 @@ def load():
     global _lib
     if _lib is not None:
         return _lib
-    path = library_path()
+    _lib = load_library(library_path())
+    return _lib
+
+
+def load_library(path: str):
+    """A ctypes handle of the library at ``path`` (e.g. the debug build) with
+    every function's signature declared; ``use_library`` makes the module's
+    calls go through it."""
     if not os.path.exists(path):
         raise ImportError(f"CUDA library not built: {path} (run paper_2506_01752_gb300.build.build())")
     lib = ctypes.CDLL(path)
@@ -128,13 +135,21 @@ def load():
         "mocd_job_footprint": (ctypes.c_int, [i64, P, i32, P]),
         "mocd_debug_inject": (ctypes.c_int, [i32, i32, i32, i32]),
         "mocd_debug_pool_usage": (ctypes.c_int, [i32, P, P]),
+        "mocd_debug_checks": (ctypes.c_int, [P, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
-    _lib = lib
     return lib
+
+
+def use_library(lib):
+    """Route this module's calls through ``lib`` (a load_library handle);
+    returns the handle used before."""
+    global _lib
+    old, _lib = _lib, lib
+    return old
 
 
 def _p(a: np.ndarray | None):
@@ -415,6 +430,16 @@ def debug_inject(site: int, skip: int = 0, count: int = 1, status: int = -8):
     """Host-side failure injection (test support): after `skip` calls at
     `site` pass, the next `count` fail; count 0 disarms."""
     _check(load().mocd_debug_inject(int(site), int(skip), int(count), int(status)), "mocd_debug_inject")
+
+
+def debug_checks(reset: bool = True):
+    """(built with checks, failures, first code, first index) of the bounds
+    checks of the debug build (all zero in the normal build)."""
+    out = np.zeros(3, dtype=np.uint64)
+    rc = load().mocd_debug_checks(_p(out), 1 if reset else 0)
+    if rc < 0:
+        raise MocdError(rc, "mocd_debug_checks")
+    return bool(rc), int(out[0]), int(out[1]), int(out[2])
 
 
 def debug_pool_usage(reset_peak: bool = False):

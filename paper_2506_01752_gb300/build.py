@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmocd.so")
 SOURCES = ["k_eval.cu", "k_variation.cu", "k_select.cu", "runtime.cu", "noalloc.cu", "server.cu", "k_stats.cu", "k_graph.cu"]
-HEADERS = ["mocd_internal.h", "philox.cuh"]
+HEADERS = ["mocd_internal.h", "philox.cuh", "mocd_check.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -35,9 +35,24 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+OUT_DEBUG = os.path.join(HERE, "_build_debug")
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=(), src_dir: str = CSRC,
-          out_dir: str = OUT) -> str:
-    """Compile ``src_dir`` into ``out_dir/libmocd.so`` (defaults: this package)."""
+          out_dir: str = None, debug: bool = False) -> str:
+    """Compile ``src_dir`` into ``out_dir/libmocd.so``.
+
+    Defaults: this package's sources into ``_build``. ``debug=True`` builds
+    the variant whose kernels check their memory accesses' invariants and
+    record failures instead of faulting (``-DMOCD_DEBUG_CHECKS``, into
+    ``_build_debug``; see mocd_debug_checks). ``src_dir``, ``out_dir`` and
+    ``extra_flags`` build a modified copy of the sources elsewhere, without
+    touching this package's own library.
+    """
+    if out_dir is None:
+        out_dir = OUT_DEBUG if debug else OUT
+    if debug:
+        extra_flags = tuple(extra_flags) + ("-DMOCD_DEBUG_CHECKS",)
     os.makedirs(out_dir, exist_ok=True)
     lib = os.path.join(out_dir, "libmocd.so")
     deps_common = [os.path.join(src_dir, h) for h in HEADERS] + [os.path.join(ROOT, "include", "mocd.h"),

@@ -33,6 +33,7 @@
 // histogram) cost a DRAM read and write-back each; done by the mutation
 // kernel, that traffic overlaps with its own work instead of stalling the
 // evaluation's row stream.
+#include "mocd_check.cuh"
 #include "mocd_internal.h"
 
 namespace mocd {
@@ -75,12 +76,13 @@ evaluate_kernel(int n, int W, int count, const int32_t *__restrict__ row_ptr,
         const int v = order ? __ldg(order + idx) : idx;
         const int beg = __ldg(row_ptr + v);
         const int end = __ldg(row_ptr + v + 1);
+        if (!MOCD_CHECK(end >= beg, kCheckRowPtr, v)) continue;  // (warp-uniform)
         const int4 own = active ? L4[(size_t)v * nq + lane] : make_int4(0, 0, 0, 0);
         for (int e0 = beg; e0 < end; e0 += 32) {
             const int cnt = min(32, end - e0);
             const int my_u = lane < cnt ? __ldg(col_idx + e0 + lane) : 0;
             // Keep the neighbours u > v of this chunk, compacted.
-            const bool up = lane < cnt && my_u > v;
+            const bool up = lane < cnt && my_u > v && MOCD_CHECK(my_u < n, kCheckNode, v);
             const unsigned upm = __ballot_sync(0xffffffffu, up);
             const int cu = __popc(upm);
             if (up) nb[__popc(upm & lt)] = my_u;
@@ -106,19 +108,19 @@ evaluate_kernel(int n, int W, int count, const int32_t *__restrict__ row_ptr,
         const unsigned long long d = (unsigned long long)(end - beg);
         if (COUNT_D && active && d > 0) {
             const unsigned dd = (unsigned)d;
-            if (i0 + 0 < count) {
+            if (i0 + 0 < count && MOCD_CHECK((unsigned)own.x < (unsigned)n, kCheckLabel, v)) {
                 const unsigned long long o = atomicAdd(hist + cell(i0 + 0, own.x), dd);
                 q0 += 2ull * o * d + d * d;
             }
-            if (i0 + 1 < count) {
+            if (i0 + 1 < count && MOCD_CHECK((unsigned)own.y < (unsigned)n, kCheckLabel, v)) {
                 const unsigned long long o = atomicAdd(hist + cell(i0 + 1, own.y), dd);
                 q1 += 2ull * o * d + d * d;
             }
-            if (i0 + 2 < count) {
+            if (i0 + 2 < count && MOCD_CHECK((unsigned)own.z < (unsigned)n, kCheckLabel, v)) {
                 const unsigned long long o = atomicAdd(hist + cell(i0 + 2, own.z), dd);
                 q2 += 2ull * o * d + d * d;
             }
-            if (i0 + 3 < count) {
+            if (i0 + 3 < count && MOCD_CHECK((unsigned)own.w < (unsigned)n, kCheckLabel, v)) {
                 const unsigned long long o = atomicAdd(hist + cell(i0 + 3, own.w), dd);
                 q3 += 2ull * o * d + d * d;
             }
@@ -230,4 +232,11 @@ cudaError_t launch_evaluate_offspring(int n, int W, int count, const int32_t *ro
     return cudaGetLastError();
 }
 
+}  // namespace mocd
+
+namespace mocd {
+cudaError_t check_record_eval(unsigned long long *out, bool reset)
+{
+    return check_record(out, reset);
+}
 }  // namespace mocd

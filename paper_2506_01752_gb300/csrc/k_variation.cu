@@ -9,6 +9,7 @@
 
 #include <utility>
 
+#include "mocd_check.cuh"
 #include "mocd_internal.h"
 #include "philox.cuh"
 
@@ -180,12 +181,15 @@ crossover_kernel(GenParams gp, const int32_t *buf0, const int32_t *buf1, int32_t
     // R index r -> position in the staged row (P half at [0, W), Q at [W, 2W)).
     for (int t = threadIdx.x; t < np; t += blockDim.x) {
         const int slot = (t & 3) * 32 + (t >> 2);
-        const int r = keep[t];
+        int r = keep[t];
+        if (!MOCD_CHECK(r >= 0 && r < 2 * np, kCheckRIndex, t)) r = 0;
         s_keep[slot] = r < np ? r : W + (r - np);
-        const int c = copy_r[t];
+        int c = copy_r[t];
+        if (!MOCD_CHECK(c >= -1 && c < 2 * np, kCheckRIndex, t)) c = 0;
         s_copy[slot] = c < 0 ? -1 : (c < np ? c : W + (c - np));
         for (int j = 0; j < E; ++j) {
-            const int p = par_r[t * kMaxParents + j];
+            int p = par_r[t * kMaxParents + j];
+            if (!MOCD_CHECK(p >= 0 && p < 2 * np, kCheckRIndex, t)) p = 0;
             s_par[(j * 4 + (t & 3)) * 32 + (t >> 2)] = p < np ? p : W + (p - np);
         }
     }
@@ -397,6 +401,13 @@ constexpr unsigned kRemovalMax = 4;
 __device__ __forceinline__ uint4 tie_words(const GenParams &gp, int v, int lane, uint32_t g)
 {
     return philox4x32_10(make_uint4((uint32_t)v, (uint32_t)lane, g, kStageMutTie), gp.key0, gp.key1);
+}
+
+// A neighbour id read from the CSR; in the debug build an id outside [0, n)
+// is recorded and replaced by 0, so that the access it feeds stays in bounds.
+__device__ __forceinline__ int checked_node(int u, int n)
+{
+    return MOCD_CHECK(u >= 0 && u < n, kCheckNode, u) ? u : 0;
 }
 
 __device__ __forceinline__ uint32_t hash_slot(int x, int hbits)
@@ -614,7 +625,7 @@ __device__ __forceinline__ int warp_mode_table(const GenParams &gp, const int32_
         int x = (int)(0x80000000u | lane);
         if (in)
             x = (tile_col && e0 + lane < kTileRows) ? tile_col[(e0 + lane) * kTileStride]
-                                                    : child[(size_t)__ldg(col_idx + beg + e0 + lane) * W + i];
+                                                    : child[(size_t)checked_node(__ldg(col_idx + beg + e0 + lane), gp.n) * W + i];
         // One insert per distinct label of the chunk, with its multiplicity.
         const unsigned peers = __match_any_sync(kFull, x);
         if (in && (peers & ((1u << lane) - 1u)) == 0) {
@@ -752,7 +763,7 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
         const int v = __ldg(order + idx);
         const int beg = __ldg(row_ptr + v);
         const int end = __ldg(row_ptr + v + 1);
-        const int deg = end - beg;
+        const int deg = MOCD_CHECK(end >= beg, kCheckRowPtr, v) ? end - beg : 0;
         int4 out = active ? C4[(size_t)v * nq + lane] : make_int4(0, 0, 0, 0);
         unsigned sel = 0;  // bit k: child 4 * lane + k mutates
         if (active && deg > 0) {
@@ -779,7 +790,7 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                 if ((sel >> k) & 1u) s_list[at++] = 4 * lane + k;
             if (active) reinterpret_cast<int4 *>(s_res)[lane] = out;
             __syncwarp();
-            const int my_u0 = lane < deg ? __ldg(col_idx + beg + lane) : 0;
+            const int my_u0 = lane < deg ? checked_node(__ldg(col_idx + beg + lane), gp.n) : 0;
             // Degree <= kTileRows: the exact per-lane votes below settle all
             // pairs at once and cost less than the Misra-Gries pass, even once
             // the population has settled. Above: the pass runs when the last
@@ -837,7 +848,7 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                 }
                 // Neighbours beyond the tile: global loads, eight in flight.
                 for (int e0 = kTileRows; use_mg && e0 < deg; e0 += 32) {
-                    const int my_u = e0 + lane < deg ? __ldg(col_idx + beg + e0 + lane) : 0;
+                    const int my_u = e0 + lane < deg ? checked_node(__ldg(col_idx + beg + e0 + lane), gp.n) : 0;
                     const int cnt = min(32, deg - e0);
                     for (int j0 = 0; j0 < cnt; j0 += 8) {
                         int xs[8];
@@ -867,7 +878,7 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                         }
                     }
                     for (int e0 = kTileRows; e0 < deg; e0 += 32) {
-                        const int my_u = e0 + lane < deg ? __ldg(col_idx + beg + e0 + lane) : 0;
+                        const int my_u = e0 + lane < deg ? checked_node(__ldg(col_idx + beg + e0 + lane), gp.n) : 0;
                         const int cnt = min(32, deg - e0);
                         for (int j0 = 0; j0 < cnt; j0 += 8) {
                             int xs[8];
@@ -1032,10 +1043,14 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
             if (deg > 0) {
                 const int i0 = 4 * lane;
                 const unsigned d = (unsigned)deg;
-                if (i0 + 0 < np && out.x >= 0) atomicAdd(hist + (size_t)out.x * W + i0 + 0, d);
-                if (i0 + 1 < np && out.y >= 0) atomicAdd(hist + (size_t)out.y * W + i0 + 1, d);
-                if (i0 + 2 < np && out.z >= 0) atomicAdd(hist + (size_t)out.z * W + i0 + 2, d);
-                if (i0 + 3 < np && out.w >= 0) atomicAdd(hist + (size_t)out.w * W + i0 + 3, d);
+                if (i0 + 0 < np && out.x >= 0 && MOCD_CHECK(out.x < gp.n, kCheckLabel, v))
+                    atomicAdd(hist + (size_t)out.x * W + i0 + 0, d);
+                if (i0 + 1 < np && out.y >= 0 && MOCD_CHECK(out.y < gp.n, kCheckLabel, v))
+                    atomicAdd(hist + (size_t)out.y * W + i0 + 1, d);
+                if (i0 + 2 < np && out.z >= 0 && MOCD_CHECK(out.z < gp.n, kCheckLabel, v))
+                    atomicAdd(hist + (size_t)out.z * W + i0 + 2, d);
+                if (i0 + 3 < np && out.w >= 0 && MOCD_CHECK(out.w < gp.n, kCheckLabel, v))
+                    atomicAdd(hist + (size_t)out.w * W + i0 + 3, d);
             }
         }
     }
@@ -1063,11 +1078,13 @@ mutation_vote_kernel(GenParams gp, int cls, const int32_t *__restrict__ row_ptr,
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         const int2 e = list[t];
         const int v = e.x, i = e.y;
+        if (!MOCD_CHECK(v >= 0 && v < gp.n && i >= 0 && i < gp.np, kCheckNode, t)) continue;
         const int beg = __ldg(row_ptr + v);
-        const int deg = __ldg(row_ptr + v + 1) - beg;
+        const int deg = min(__ldg(row_ptr + v + 1) - beg, N);
         int x[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) x[j] = j < deg ? child[(size_t)__ldg(col_idx + beg + j) * W + i] : INT_MAX;
+        for (int j = 0; j < N; ++j)
+            x[j] = j < deg ? child[(size_t)checked_node(__ldg(col_idx + beg + j), gp.n) * W + i] : INT_MAX;
         sort_network<N>(x);
         // The longest run length among the deg real entries and the mask of
         // the positions where a run of that length ends.
@@ -1126,7 +1143,7 @@ mutation_vote_kernel(GenParams gp, int cls, const int32_t *__restrict__ row_ptr,
 #pragma unroll
         for (int j = 1; j < N; ++j) res = pos == j ? x[j] : res;
         q[(size_t)v * W + i] = res;
-        atomicAdd(hist + (size_t)res * W + i, (unsigned)deg);
+        if (MOCD_CHECK(res >= 0 && res < gp.n, kCheckLabel, v)) atomicAdd(hist + (size_t)res * W + i, (unsigned)deg);
         if (4 * best > deg) atomicAdd(hint + v, 1u);
     }
 }
@@ -1152,14 +1169,15 @@ mutation_hub_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int
     for (int t = warp; t < total; t += nwarps) {
         const int2 e = list[t];
         const int v = e.x, i = e.y;
+        if (!MOCD_CHECK(v >= 0 && v < gp.n && i >= 0 && i < gp.np, kCheckNode, t)) continue;  // (warp-uniform)
         const int beg = __ldg(row_ptr + v);
-        const int deg = __ldg(row_ptr + v + 1) - beg;
+        const int deg = min(__ldg(row_ptr + v + 1) - beg, gp.hub_hs / 2);
         const uint4 r = philox4x32_10(make_uint4((uint32_t)v, (uint32_t)(i >> 2), g, kStageMutTie), gp.key0, gp.key1);
         unsigned mx = 0;
         const int lab = warp_mode_table(gp, child, col_idx, beg, deg, nullptr, i, hkey, hcnt, word_of(r, i & 3), mx);
         if (lane == 0) {
             q[(size_t)v * gp.W + i] = lab;
-            atomicAdd(hist + (size_t)lab * gp.W + i, (unsigned)deg);
+            if (MOCD_CHECK(lab >= 0 && lab < gp.n, kCheckLabel, v)) atomicAdd(hist + (size_t)lab * gp.W + i, (unsigned)deg);
             if (4 * (int)mx > deg) atomicAdd(hint + v, 1u);
         }
     }
@@ -1278,4 +1296,11 @@ cudaError_t launch_mutation(const GenParams &gp, const PopState &ps, const int32
     return e;
 }
 
+}  // namespace mocd
+
+namespace mocd {
+cudaError_t check_record_variation(unsigned long long *out, bool reset)
+{
+    return check_record(out, reset);
+}
 }  // namespace mocd

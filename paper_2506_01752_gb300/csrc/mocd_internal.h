@@ -134,6 +134,11 @@ cudaError_t launch_to_node_major(int n, int W, int count, const int32_t *src, in
 // sorted, in range and free of self loops (checked on the host first).
 cudaError_t launch_symmetry_check(int n, const int32_t *row_ptr, const int32_t *col_idx, int *bad, int sms,
                                   cudaStream_t s);
+// Debug-build bounds-check records of the kernel translation units
+// (mocd_check.cuh): out[3] = failures, first code, first index.
+cudaError_t check_record_eval(unsigned long long *out, bool reset);
+cudaError_t check_record_variation(unsigned long long *out, bool reset);
+
 // Occupancy-derived grid sizes.
 // Resident blocks of the evaluation kernel in the given histogram layout.
 int grid_for_eval(int sms, bool label_major = true);

@@ -1303,6 +1303,22 @@ int mocd_debug_inject(int32_t site, int32_t skip, int32_t count, int32_t status)
     return MOCD_OK;
 }
 
+int mocd_debug_checks(uint64_t *out, int32_t reset)
+{
+    if (!out) return MOCD_ERR_INVALID_ARG;
+    unsigned long long a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
+    CK(check_record_eval(a, reset != 0));
+    CK(check_record_variation(b, reset != 0));
+    out[0] = a[0] + b[0];
+    out[1] = a[0] ? a[1] : b[1];
+    out[2] = a[0] ? a[2] : b[2];
+#ifdef MOCD_DEBUG_CHECKS
+    return 1;
+#else
+    return 0;
+#endif
+}
+
 int mocd_debug_pool_usage(int32_t reset_peak, int64_t *current, int64_t *peak)
 {
     int dev = 0;

@@ -131,3 +131,11 @@ def test_large_graph_first_failing_row_decides(lib, defect):
         ci[rp[hi]:rp[hi + 1]] = seg[::-1]
         want = -4
     assert _upload_status(rp, ci) == want
+
+
+def test_debug_build_loads_and_exports_every_symbol():
+    """The bounds-checked variant (-DMOCD_DEBUG_CHECKS) builds and exports
+    the same C ABI."""
+    lib = mocd.load_library(cuda_build.build(debug=True))
+    for name in declared_functions():
+        assert hasattr(lib, name), name
