@@ -755,7 +755,7 @@ def run_serve(args):
         "config": {"workload": "Poisson 20/s; LFR-style graphs, n log-spaced 1e3-1e6 (12-graph pool), "
                                "mu U[0.1,0.6]; N_p=100, G=100",
                    "hbm_budget_gb": args.hbm_budget_gb, "max_running": args.max_running, "depth": args.depth,
-                   "admission": "shortest work first" if args.policy else "first come first served",
+                   "admission": "highest response ratio next" if args.policy else "first come first served",
                    "admission_threads": 2,
                    "pool": [d for _, _, d in pool]},
         "n_gpus": 1, "dtype": "int32", "data": "synthetic", "clocks": clocks,
