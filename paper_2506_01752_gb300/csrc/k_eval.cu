@@ -26,9 +26,9 @@
 // which writes every child's final label of node v, adds deg(v) to the
 // label-major cell of that label as it goes (fire-and-forget reductions that
 // overlap its own latency-bound work). The evaluation of the offspring then
-// counts intra only (COUNT_D = false), and square_sum_kernel forms
-// S = sum_c D_c^2 in one coalesced sweep of the histogram, zeroing it for the
-// next generation. While the labels are still nearly all distinct, the N_p n
+// counts intra (COUNT_D = false) and, in the same launch once a warp's nodes
+// are done, forms S = sum_c D_c^2 in a coalesced sweep of the histogram rows,
+// zeroing them for the next generation. While the labels are still nearly all distinct, the N_p n
 // histogram additions land on different sectors, which at n = 10^6 (a 400 MB
 // histogram) cost a DRAM read and write-back each; done by the mutation
 // kernel, that traffic overlaps with its own work instead of stalling the
@@ -127,36 +127,12 @@ evaluate_kernel(int n, int W, int count, const int32_t *__restrict__ row_ptr,
         }
     }
 
-    if (active) {
-        if (i0 + 0 < count) { atomicAdd(&s_intra[i0 + 0], (unsigned long long)c0); if (COUNT_D) atomicAdd(&s_sq[i0 + 0], q0); }
-        if (i0 + 1 < count) { atomicAdd(&s_intra[i0 + 1], (unsigned long long)c1); if (COUNT_D) atomicAdd(&s_sq[i0 + 1], q1); }
-        if (i0 + 2 < count) { atomicAdd(&s_intra[i0 + 2], (unsigned long long)c2); if (COUNT_D) atomicAdd(&s_sq[i0 + 2], q2); }
-        if (i0 + 3 < count) { atomicAdd(&s_intra[i0 + 3], (unsigned long long)c3); if (COUNT_D) atomicAdd(&s_sq[i0 + 3], q3); }
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < count; t += blockDim.x) {
-        if (s_intra[t]) atomicAdd(acc + t, s_intra[t]);
-        if (s_sq[t]) atomicAdd(acc + kMaxPop + t, s_sq[t]);
-    }
-}
-
-// S_i = sum_c hist[c][i]^2 for the label-major histogram [n][W] (a warp per
-// row, lane q the int4 of individuals 4q..4q+3), zeroing every cell it finds
-// non-zero. D_c^2 < 2^62 and the sum is at most (2m)^2, so the 64-bit sums
-// are exact.
-__global__ void __launch_bounds__(kBlock)
-square_sum_kernel(int n, int W, int count, uint32_t *__restrict__ hist, unsigned long long *__restrict__ acc)
-{
-    __shared__ unsigned long long s_sq[kMaxPop];
-    for (int t = threadIdx.x; t < kMaxPop; t += blockDim.x) s_sq[t] = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int nq = W >> 2;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    uint4 *__restrict__ H4 = reinterpret_cast<uint4 *>(hist);
-    unsigned long long q0 = 0, q1 = 0, q2 = 0, q3 = 0;
-    if (lane < nq) {
+    if (!COUNT_D && LABEL_MAJOR && active) {
+        // S from the histogram [n][W] that the mutation kernel built: a warp
+        // per row, lane q the int4 of individuals 4q..4q+3; every non-zero
+        // cell is squared and cleared. D_c^2 < 2^62 and S <= (2m)^2, so the
+        // 64-bit sums are exact.
+        uint4 *__restrict__ H4 = reinterpret_cast<uint4 *>(hist);
         for (int c = warp; c < n; c += nwarps) {
             const size_t at = (size_t)c * nq + lane;
             const uint4 x = H4[at];
@@ -168,15 +144,18 @@ square_sum_kernel(int n, int W, int count, uint32_t *__restrict__ hist, unsigned
                 H4[at] = make_uint4(0, 0, 0, 0);
             }
         }
-        const int i0 = 4 * lane;
-        if (q0 && i0 + 0 < count) atomicAdd(&s_sq[i0 + 0], q0);
-        if (q1 && i0 + 1 < count) atomicAdd(&s_sq[i0 + 1], q1);
-        if (q2 && i0 + 2 < count) atomicAdd(&s_sq[i0 + 2], q2);
-        if (q3 && i0 + 3 < count) atomicAdd(&s_sq[i0 + 3], q3);
+    }
+    if (active) {
+        if (i0 + 0 < count) { atomicAdd(&s_intra[i0 + 0], (unsigned long long)c0); atomicAdd(&s_sq[i0 + 0], q0); }
+        if (i0 + 1 < count) { atomicAdd(&s_intra[i0 + 1], (unsigned long long)c1); atomicAdd(&s_sq[i0 + 1], q1); }
+        if (i0 + 2 < count) { atomicAdd(&s_intra[i0 + 2], (unsigned long long)c2); atomicAdd(&s_sq[i0 + 2], q2); }
+        if (i0 + 3 < count) { atomicAdd(&s_intra[i0 + 3], (unsigned long long)c3); atomicAdd(&s_sq[i0 + 3], q3); }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < count; t += blockDim.x)
+    for (int t = threadIdx.x; t < count; t += blockDim.x) {
+        if (s_intra[t]) atomicAdd(acc + t, s_intra[t]);
         if (s_sq[t]) atomicAdd(acc + kMaxPop + t, s_sq[t]);
+    }
 }
 
 }  // namespace
@@ -200,14 +179,6 @@ int grid_for_eval_intra(int sms)
     return sms * per_sm;
 }
 
-int grid_for_square_sum(int sms)
-{
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, square_sum_kernel, kBlock, 0);
-    if (per_sm < 1) per_sm = 1;
-    return sms * per_sm;
-}
-
 cudaError_t launch_evaluate(int n, int W, int count, const int32_t *row_ptr, const int32_t *col_idx,
                             const int32_t *labels, uint32_t *hist, unsigned long long *acc,
                             int grid, cudaStream_t s, const int32_t *order, bool label_major)
@@ -223,12 +194,9 @@ cudaError_t launch_evaluate(int n, int W, int count, const int32_t *row_ptr, con
 
 cudaError_t launch_evaluate_offspring(int n, int W, int count, const int32_t *row_ptr, const int32_t *col_idx,
                                       const int32_t *labels, uint32_t *hist, unsigned long long *acc,
-                                      int grid, int sq_grid, cudaStream_t s, const int32_t *order)
+                                      int grid, cudaStream_t s, const int32_t *order)
 {
     evaluate_kernel<true, false><<<grid, kBlock, 0, s>>>(n, W, count, row_ptr, col_idx, labels, hist, acc, order);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    square_sum_kernel<<<sq_grid, kBlock, 0, s>>>(n, W, count, hist, acc);
     return cudaGetLastError();
 }
 

@@ -143,14 +143,13 @@ cudaError_t check_record_variation(unsigned long long *out, bool reset);
 // Resident blocks of the evaluation kernel in the given histogram layout.
 int grid_for_eval(int sms, bool label_major = true);
 int grid_for_eval_intra(int sms);
-int grid_for_square_sum(int sms);
 // Objectives of the offspring inside a generation: the mutation kernel has
 // already added every child's degrees to the label-major histogram (and
-// cleared acc); this counts intra, then forms S from the histogram and zeroes
-// it.
+// cleared acc); one launch counts intra, then forms S from the histogram and
+// zeroes it.
 cudaError_t launch_evaluate_offspring(int n, int W, int count, const int32_t *row_ptr, const int32_t *col_idx,
                                       const int32_t *labels, uint32_t *hist, unsigned long long *acc,
-                                      int grid, int sq_grid, cudaStream_t s, const int32_t *order);
+                                      int grid, cudaStream_t s, const int32_t *order);
 int grid_for_crossover(int sms, int es);
 int grid_for_mutation(int sms, int hash_size, int *smem_bytes);
 int mutation_warps_per_block();

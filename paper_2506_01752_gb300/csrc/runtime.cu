@@ -55,9 +55,9 @@ struct mocd_ctx {
     size_t hub_cap = 0;     // entries of ps.hub_table
     void *d_small = nullptr;
     int grid_eval = 0, grid_cross = 0, grid_mut = 0;
-    int grid_eval_intra = 0, grid_square = 0, grid_vote = 0;
+    int grid_eval_intra = 0, grid_vote = 0;
     int occ_eval = 0, occ_cross = 0, occ_mut = 0;  // occupancy-limited grids
-    int occ_eval_intra = 0, occ_square = 0;
+    int occ_eval_intra = 0;
     int nodes_per_warp = 1;                         // launch shape (autotuned for batches)
     int32_t host_gen = 0;   // generations run since init
     int32_t version = 0;    // bumped whenever the population is (re)built
@@ -195,7 +195,6 @@ void size_grids(mocd_ctx *c)
     };
     c->grid_eval = shape(c->occ_eval, kBlock / 32);
     c->grid_eval_intra = shape(c->occ_eval_intra, kBlock / 32);
-    c->grid_square = shape(c->occ_square, kBlock / 32);
     c->grid_cross = shape(c->occ_cross, kBlock / 32);
     c->grid_mut = shape(c->occ_mut, mutation_warps_per_block());
 }
@@ -312,7 +311,6 @@ int prepare_population(mocd_ctx *c, const mocd_params *p)
     gp.thr_m = (unsigned long long)floor(p->p_mutation * 4294967296.0);
     c->occ_eval = grid_for_eval(c->sms);
     c->occ_eval_intra = grid_for_eval_intra(c->sms);
-    c->occ_square = grid_for_square_sum(c->sms);
     c->grid_vote = grid_for_vote(c->sms);
     c->occ_cross = grid_for_crossover(c->sms, gp.es);
     int smem = 0;
@@ -347,7 +345,7 @@ int issue_generation(mocd_ctx *c, cudaStream_t st, bool events, bool with_select
     CK(launch_mutation(gp, ps, c->d_row_ptr, c->d_col_idx, c->d_order, c->grid_mut, c->grid_vote, st));
     if (events) CK(mark(c, 2, st));
     CK(launch_evaluate_offspring(gp.n, gp.W, gp.np, c->d_row_ptr, c->d_col_idx, ps.q, ps.hist, ps.acc,
-                                 c->grid_eval_intra, c->grid_square, st, c->d_order));
+                                 c->grid_eval_intra, st, c->d_order));
     if (events) CK(mark(c, 3, st));
     if (!with_select) return MOCD_OK;  // a batch selects all its members in one launch
     CK(launch_select(gp, ps, 1, st));
