@@ -1257,18 +1257,18 @@ int grid_for_mutation(int sms, int hash_size, int *smem_bytes)
     return sms * per_sm;
 }
 
-int grid_for_vote(int sms)
+void grid_for_votes(int sms, int *grid64, int *grid128)
 {
     int a = 0, b = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, mutation_vote_kernel<2 * kTileRows>, kMutBlock, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, mutation_vote_kernel<kDeferMax>, kMutBlock, 0);
-    a = a < 1 ? 1 : a;
-    b = b < 1 ? 1 : b;
-    return sms * (a < b ? a : b);
+    *grid64 = sms * (a < 1 ? 1 : a);
+    *grid128 = sms * (b < 1 ? 1 : b);
 }
 
 cudaError_t launch_mutation(const GenParams &gp, const PopState &ps, const int32_t *row_ptr,
-                            const int32_t *col_idx, const int32_t *order, int grid, int vote_grid, cudaStream_t s)
+                            const int32_t *col_idx, const int32_t *order, int grid, int grid64, int grid128,
+                            cudaStream_t s)
 {
     mutation_kernel<<<grid, kMutBlock, mutation_smem(gp.hash_size), s>>>(gp, row_ptr, col_idx, order, ps.c, ps.q,
                                                                        ps.gen, ps.hist, ps.acc, ps.hint, ps.dlist,
@@ -1276,14 +1276,14 @@ cudaError_t launch_mutation(const GenParams &gp, const PopState &ps, const int32
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (gp.defer_cap[0] > 0) {
-        mutation_vote_kernel<2 * kTileRows><<<vote_grid, kMutBlock, 0, s>>>(gp, 0, row_ptr, col_idx, ps.c, ps.q,
+        mutation_vote_kernel<2 * kTileRows><<<grid64, kMutBlock, 0, s>>>(gp, 0, row_ptr, col_idx, ps.c, ps.q,
                                                                            ps.gen, ps.hist, ps.hint, ps.dlist,
                                                                            ps.dcount);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     if (gp.defer_cap[1] > 0) {
-        mutation_vote_kernel<kDeferMax><<<vote_grid, kMutBlock, 0, s>>>(gp, 1, row_ptr, col_idx, ps.c, ps.q, ps.gen,
+        mutation_vote_kernel<kDeferMax><<<grid128, kMutBlock, 0, s>>>(gp, 1, row_ptr, col_idx, ps.c, ps.q, ps.gen,
                                                                         ps.hist, ps.hint, ps.dlist, ps.dcount);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;

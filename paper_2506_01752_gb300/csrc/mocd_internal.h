@@ -100,8 +100,11 @@ cudaError_t launch_crossover(const GenParams &gp, const PopState &ps, int grid, 
 // order: the nodes in the sequence the grid-stride loop visits them
 // (degree descending), or NULL for 0..n-1 (evaluation only).
 cudaError_t launch_mutation(const GenParams &gp, const PopState &ps, const int32_t *row_ptr,
-                            const int32_t *col_idx, const int32_t *order, int grid, int vote_grid, cudaStream_t s);
-int grid_for_vote(int sms);
+                            const int32_t *col_idx, const int32_t *order, int grid, int grid64, int grid128,
+                            cudaStream_t s);
+// Resident-block grids of the two per-pair vote kernels (degree classes
+// 33..64 and 65..128).
+void grid_for_votes(int sms, int *grid64, int *grid128);
 // hist: label-major [n][W] (label_major) or individual-major [count][n],
 // zeroed by the caller.
 cudaError_t launch_evaluate(int n, int W, int count, const int32_t *row_ptr, const int32_t *col_idx,

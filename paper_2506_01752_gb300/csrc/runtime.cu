@@ -55,7 +55,7 @@ struct mocd_ctx {
     size_t hub_cap = 0;     // entries of ps.hub_table
     void *d_small = nullptr;
     int grid_eval = 0, grid_cross = 0, grid_mut = 0;
-    int grid_eval_intra = 0, grid_vote = 0;
+    int grid_eval_intra = 0, grid_vote64 = 0, grid_vote128 = 0;
     int occ_eval = 0, occ_cross = 0, occ_mut = 0;  // occupancy-limited grids
     int occ_eval_intra = 0;
     int nodes_per_warp = 1;                         // launch shape (autotuned for batches)
@@ -311,7 +311,7 @@ int prepare_population(mocd_ctx *c, const mocd_params *p)
     gp.thr_m = (unsigned long long)floor(p->p_mutation * 4294967296.0);
     c->occ_eval = grid_for_eval(c->sms);
     c->occ_eval_intra = grid_for_eval_intra(c->sms);
-    c->grid_vote = grid_for_vote(c->sms);
+    grid_for_votes(c->sms, &c->grid_vote64, &c->grid_vote128);
     c->occ_cross = grid_for_crossover(c->sms, gp.es);
     int smem = 0;
     c->occ_mut = grid_for_mutation(c->sms, gp.hash_size, &smem);
@@ -342,7 +342,8 @@ int issue_generation(mocd_ctx *c, cudaStream_t st, bool events, bool with_select
     if (events) CK(mark(c, 0, st));
     CK(launch_crossover(gp, ps, c->grid_cross, st));
     if (events) CK(mark(c, 1, st));
-    CK(launch_mutation(gp, ps, c->d_row_ptr, c->d_col_idx, c->d_order, c->grid_mut, c->grid_vote, st));
+    CK(launch_mutation(gp, ps, c->d_row_ptr, c->d_col_idx, c->d_order, c->grid_mut, c->grid_vote64,
+                       c->grid_vote128, st));
     if (events) CK(mark(c, 2, st));
     CK(launch_evaluate_offspring(gp.n, gp.W, gp.np, c->d_row_ptr, c->d_col_idx, ps.q, ps.hist, ps.acc,
                                  c->grid_eval_intra, st, c->d_order));
