@@ -429,6 +429,7 @@ def run_mine(args):
     stream = torch.cuda.Stream(device=dev)
     ctx = mocd.graph_upload(rp, ci, stream)
     mocd.population_init(ctx, params)
+    kernels_per_generation = mocd.generation_kernels(ctx)
     mocd.set_timing(ctx, True)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -544,7 +545,7 @@ def run_mine(args):
             "roofline_hbm": large,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": kernels_per_generation * args.steps,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

@@ -409,14 +409,25 @@ int mocd_synchronize(mocd_ctx *ctx);
  * Per-kernel timing of the generation step (measurement support, not part
  * of the method): when enabled, the generation graph records CUDA events
  * between its kernels. mocd_kernel_times writes, for the most recent
- * generation, the duration in milliseconds of each kernel, in this order:
- * crossover, mutation (which also clears the evaluation histogram),
- * evaluation, selection; returns the number of stages (4) or a negative
- * status. NOT_READY if timing is off or no generation ran since it was
- * enabled.
+ * generation, the duration in milliseconds of each stage, in this order:
+ * crossover, mutation (its main kernel plus the per-pair vote kernels of
+ * the graph's degree classes; it also builds the degree histogram of the
+ * children), evaluation (which squares and clears that histogram),
+ * selection; returns the number of stages (4) or a negative status.
+ * NOT_READY if timing is off or no generation ran since it was enabled.
  */
 int mocd_set_timing(mocd_ctx *ctx, int32_t enable);
 int mocd_kernel_times(mocd_ctx *ctx, float *ms, int32_t cap);
+
+/*
+ * Number of kernel launches in one generation (measurement support): the
+ * kernel nodes of the captured generation graph without timing events.
+ * It depends on the graph: crossover, mutation, evaluation and selection,
+ * plus one per-pair vote kernel for each degree class the graph has
+ * (33..64, 65..128, above 512). Captures the graph if it does not exist
+ * yet. NOT_READY before initialisation.
+ */
+int mocd_generation_kernels(mocd_ctx *ctx, int32_t *kernels);
 
 /* Graph size and population shape: any pointer may be NULL. */
 int mocd_info(mocd_ctx *ctx, int64_t *n, int64_t *m, int32_t *pop_size, int32_t *generation);

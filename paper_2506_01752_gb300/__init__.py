@@ -114,6 +114,7 @@ def load_library(path: str):
         "mocd_set_timing": (ctypes.c_int, [P, i32]),
         "mocd_kernel_times": (ctypes.c_int, [P, P, i32]),
         "mocd_info": (ctypes.c_int, [P, P, P, P, P]),
+        "mocd_generation_kernels": (ctypes.c_int, [P, P]),
         "mocd_destroy": (None, [P]),
         "mocd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
         "mocd_evaluate_noalloc": (ctypes.c_int, [P, P, i64, P, i32, P, P, P]),
@@ -200,6 +201,13 @@ def info(ctx):
     _check(load().mocd_info(ctx, ctypes.byref(n), ctypes.byref(m), ctypes.byref(np_), ctypes.byref(g)),
            "mocd_info")
     return dict(n=n.value, m=m.value, pop_size=np_.value, generation=g.value)
+
+
+def generation_kernels(ctx) -> int:
+    """Kernel launches in one generation of this context's graph."""
+    k = ctypes.c_int32()
+    _check(load().mocd_generation_kernels(ctx, ctypes.byref(k)), "mocd_generation_kernels")
+    return k.value
 
 
 def pareto_front(ctx, with_labels: bool = True) -> Front:

@@ -860,6 +860,30 @@ int mocd_generation(mocd_ctx *c, int32_t n_generations)
     return MOCD_OK;
 }
 
+int mocd_generation_kernels(mocd_ctx *c, int32_t *kernels)
+{
+    if (!c || !kernels) return MOCD_ERR_INVALID_ARG;
+    if (!c->ready) return MOCD_ERR_NOT_READY;
+    CK(cudaSetDevice(c->device));
+    const bool timing = c->timing;
+    c->timing = false;
+    const int rc = build_graph(c);
+    c->timing = timing;
+    if (rc) return rc;
+    size_t count = 0;
+    CK(cudaGraphGetNodes(c->graph[0], nullptr, &count));
+    std::vector<cudaGraphNode_t> nodes(count);
+    CK(cudaGraphGetNodes(c->graph[0], nodes.data(), &count));
+    int32_t k = 0;
+    for (size_t t = 0; t < count; ++t) {
+        cudaGraphNodeType type;
+        CK(cudaGraphNodeGetType(nodes[t], &type));
+        if (type == cudaGraphNodeTypeKernel) ++k;
+    }
+    *kernels = k;
+    return MOCD_OK;
+}
+
 int mocd_front_stats(mocd_ctx *c, int32_t cap, int32_t *count, int64_t *communities, int64_t *size_sumsq,
                      double *mean_conductance, double *max_conductance)
 {

@@ -373,6 +373,25 @@ def test_kernel_timing_reports_every_stage():
     assert np.array_equal(a[0], b[0])
 
 
+@pytest.mark.parametrize("degrees,expect", [
+    ((5, 20, 32), 4),          # crossover, mutation, evaluation, selection
+    ((5, 40), 5),              # + the degree 33..64 vote kernel
+    ((100,), 5),               # + the degree 65..128 vote kernel
+    ((300,), 4),               # 129..512: the mutation kernel's shared table
+    ((600,), 5),               # + the hub kernel above 512
+    ((40, 100, 300, 600), 7),  # every class at once
+])
+def test_generation_kernel_count(degrees, expect):
+    rp, ci = degree_ladder(degrees)
+    with Ctx(rp, ci) as h:
+        mocd.population_init(h, mocd.Params())
+        mocd.set_timing(h, True)
+        assert mocd.generation_kernels(h) == expect
+        # counting captures the plain graph only; the timing graph still runs
+        mocd.generation(h, 1)
+        assert set(mocd.kernel_times(h)) == set(mocd.STAGES)
+
+
 def test_timing_toggled_every_generation_matches_oracle():
     """The plain and the stage-timed generation graphs coexist; switching
     between them every generation (as the benchmark does) changes nothing in
