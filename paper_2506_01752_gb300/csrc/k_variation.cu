@@ -518,32 +518,51 @@ __device__ __forceinline__ void sort_network(int (&x)[N])
     apply_network<N>(x, std::make_index_sequence<MergeExchange<N>::C>{});
 }
 
+// x[pos] for a run-time pos < N without indexing the register array: a
+// tree of selects on the bits of pos, one level per bit (LEN live entries).
+template <int N, int LEN, int B>
+__device__ __forceinline__ void select_level(int (&y)[N], int pos)
+{
+    if constexpr (LEN > 1) {
+        const bool hi = (pos >> B) & 1;
+#pragma unroll
+        for (int k = 0; k < (LEN + 1) / 2; ++k) y[k] = (2 * k + 1 < LEN && hi) ? y[2 * k + 1] : y[2 * k];
+        select_level<N, (LEN + 1) / 2, B + 1>(y, pos);
+    }
+}
+
+template <int N>
+__device__ __forceinline__ int select_at(const int (&x)[N], int pos)
+{
+    int y[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) y[j] = x[j];
+    select_level<N, N, 0>(y, pos);
+    return y[0];
+}
+
 // Exact neighbour-majority of one pair by its own lane: the pair's deg <= N
-// labels (column `col` of the staged tile) are sorted in registers; equal
-// labels then form runs, the longest runs are the tied labels in ascending
-// order, and the pick(u, t)-th of them is the result.
+// labels (1 <= deg <= N <= 32) are sorted in registers; equal labels then
+// form runs, the longest runs are the tied labels in ascending order, and the
+// pick(u, t)-th of them is the result. Bit j of e is set when entries j and
+// j + 1 are equal, so a run of L labels is L - 1 consecutive set bits; each
+// step m &= m >> 1 shortens every run of set bits by one, and the last
+// non-zero m has one bit per longest run, at its first entry (all entries
+// when no two labels are equal).
 template <int N>
 __device__ __forceinline__ int lane_pick(int (&x)[N], int deg, uint32_t u)
 {
     sort_network<N>(x);
-    // One pass: the longest run length among the deg real entries and the
-    // mask of the positions where a run of that length ends.
-    int run = 0, best = 0;
-    unsigned ends = 0;
+    unsigned e = 0;
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-        run = (j > 0 && x[j] == x[j - 1]) ? run + 1 : 1;
-        const bool last = j < deg && (j + 1 == deg || (j + 1 < N && x[j + 1] != x[j]));
-        if (last && run > best) {
-            best = run;
-            ends = 0;
-        }
-        if (last && run == best) ends |= 1u << j;
-    }
-    const int t = __popc(ends);
+    for (int j = 0; j + 1 < N; ++j) e |= (x[j] == x[j + 1] ? 1u : 0u) << j;
+    e &= deg >= 2 ? 0xffffffffu >> (33 - deg) : 0u;  // pairs (j, j + 1) with j + 1 < deg
+    unsigned starts = deg >= 32 ? 0xffffffffu : (1u << deg) - 1u;
+    for (unsigned m = e; m != 0u; m &= m >> 1) starts = m;
+    const int t = __popc(starts);
     const unsigned kk = t > 1 ? pick_index(u, (uint32_t)t) : 0u;
-    // Position of the kk-th set bit of `ends`, halving the window each step.
-    unsigned m = ends, k = kk;
+    // Position of the kk-th set bit of `starts`, halving the window each step.
+    unsigned m = starts, k = kk;
     int pos = 0;
 #pragma unroll
     for (int w = 16; w >= 1; w >>= 1) {
@@ -557,10 +576,7 @@ __device__ __forceinline__ int lane_pick(int (&x)[N], int deg, uint32_t u)
             m = low;
         }
     }
-    int res = x[0];
-#pragma unroll
-    for (int j = 1; j < N; ++j) res = pos == j ? x[j] : res;
-    return res;
+    return select_at<N>(x, pos);
 }
 
 // Lane-parallel exact vote of every selected pair of a node with
@@ -1086,62 +1102,74 @@ mutation_vote_kernel(GenParams gp, int cls, const int32_t *__restrict__ row_ptr,
         for (int j = 0; j < N; ++j)
             x[j] = j < deg ? child[(size_t)checked_node(__ldg(col_idx + beg + j), gp.n) * W + i] : INT_MAX;
         sort_network<N>(x);
-        // The longest run length among the deg real entries and the mask of
-        // the positions where a run of that length ends.
-        int run = 0, best = 0;
-        unsigned long long ends[NW];
+        // Runs of equal labels as in lane_pick, over NW 64-bit words: bit j
+        // of eq is set when entries j and j + 1 (< deg) are equal; each step
+        // m &= m >> 1 (across words) shortens every run of set bits by one,
+        // and the last non-zero m marks the first entry of each longest run.
+        unsigned long long eq[NW], starts[NW], m[NW];
 #pragma unroll
-        for (int w = 0; w < NW; ++w) ends[w] = 0ull;
+        for (int w = 0; w < NW; ++w) eq[w] = 0ull;
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-            run = (j > 0 && x[j] == x[j - 1]) ? run + 1 : 1;
-            const bool last = j < deg && (j + 1 == deg || (j + 1 < N && x[j + 1] != x[j]));
-            if (last && run > best) {
-                best = run;
+        for (int j = 0; j + 1 < N; ++j) eq[j >> 6] |= (x[j] == x[j + 1] ? 1ull : 0ull) << (j & 63);
+        bool any = false;
 #pragma unroll
-                for (int w = 0; w < NW; ++w) ends[w] = 0ull;
+        for (int w = 0; w < NW; ++w) {
+            const int pairs = deg - 1 - 64 * w;  // valid bits of word w
+            const int ents = deg - 64 * w;
+            eq[w] &= pairs >= 64 ? ~0ull : pairs <= 0 ? 0ull : (1ull << pairs) - 1ull;
+            starts[w] = ents >= 64 ? ~0ull : ents <= 0 ? 0ull : (1ull << ents) - 1ull;
+            m[w] = eq[w];
+            any |= eq[w] != 0ull;
+        }
+        int best = 1;
+        while (any) {
+            any = false;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                starts[w] = m[w];
+                const unsigned long long carry = w + 1 < NW ? m[w + 1 < NW ? w + 1 : w] << 63 : 0ull;
+                m[w] &= (m[w] >> 1) | carry;
+                any |= m[w] != 0ull;
             }
-            if (last && run == best) ends[j >> 6] |= 1ull << (j & 63);
+            ++best;
         }
         int tcount = 0;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) tcount += __popcll(ends[w]);
+        for (int w = 0; w < NW; ++w) tcount += __popcll(starts[w]);
         unsigned kk = 0;
         if (tcount > 1) {
             const uint4 r = philox4x32_10(make_uint4((uint32_t)v, (uint32_t)(i >> 2), g, kStageMutTie), gp.key0,
                                           gp.key1);
             kk = pick_index(word_of(r, i & 3), (uint32_t)tcount);
         }
-        // Position of the kk-th set bit of the ends mask.
+        // Position of the kk-th set bit of the starts mask.
         int pos = 0;
         unsigned k = kk;
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
-            const unsigned c = (unsigned)__popcll(ends[w]);
+            const unsigned c = (unsigned)__popcll(starts[w]);
             if (k >= c) {
                 k -= c;
                 continue;
             }
-            unsigned long long m = ends[w];
+            unsigned long long mm = starts[w];
             int p = 64 * w;
 #pragma unroll
             for (int width = 32; width >= 1; width >>= 1) {
-                const unsigned long long low = m & ((1ull << width) - 1ull);
+                const unsigned long long low = mm & ((1ull << width) - 1ull);
                 const unsigned lc = (unsigned)__popcll(low);
                 if (k >= lc) {
                     k -= lc;
-                    m >>= width;
+                    mm >>= width;
                     p += width;
                 } else {
-                    m = low;
+                    mm = low;
                 }
             }
             pos = p;
             break;
         }
-        int res = x[0];
-#pragma unroll
-        for (int j = 1; j < N; ++j) res = pos == j ? x[j] : res;
+        const int res = select_at<N>(x, pos);
         q[(size_t)v * W + i] = res;
         if (MOCD_CHECK(res >= 0 && res < gp.n, kCheckLabel, v)) atomicAdd(hist + (size_t)res * W + i, (unsigned)deg);
         if (4 * best > deg) atomicAdd(hint + v, 1u);
