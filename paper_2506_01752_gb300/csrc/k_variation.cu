@@ -342,9 +342,10 @@ crossover_kernel(GenParams gp, const int32_t *buf0, const int32_t *buf1, int32_t
 // pairs at a time (one neighbour per lane grouped by __match_any_sync, the
 // pick(u, t)-th tied label by removing minima or, for deep ranks, by sorting
 // the tied labels across the warp). Degree > 32: when the node's history says
-// it pays, a three-counter Misra-Gries summary and an exact recount of its
-// survivors settle every pair whose best count c has 4 c > deg (every label
-// reaching c is then a candidate); the other pairs of degree 33..kDeferMax
+// it pays, a Misra-Gries summary with K counters (K = 1 up to degree 64, 3
+// above) and an exact recount of its survivors settle every pair whose best
+// count c has (K + 1) c > deg (every label reaching c is then a candidate);
+// the other pairs of degree 33..kDeferMax
 // are listed for mutation_vote_kernel (one pair per thread, labels sorted in
 // registers), and those of higher degree take a count table in shared
 // memory, one pair at a time.
@@ -811,8 +812,9 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
             // pairs at once and cost less than the Misra-Gries pass, even once
             // the population has settled. Above: the pass runs when the last
             // generation's exact results (whichever path produced them) say
-            // that most of v's pairs had a label above deg / 4, the pairs the
-            // pass settles. hint = (pairs << 16) | such pairs; 0: no history.
+            // that most of v's pairs had a label above deg / (K + 1), the pairs
+            // the pass settles. hint = (pairs << 16) | such pairs; 0: no
+            // history.
             const uint32_t h = deg > kTileRows ? hint[v] : 0u;
             const bool use_mg = deg > kTileRows && (h == 0u || 2u * (h & 0xffffu) >= (h >> 16));
             const bool deferred_class = (deg > kTileRows && deg <= kDeferMax) || deg > kSharedTableMax;
@@ -823,28 +825,6 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                 // Lane = pair (selected child i of node v).
                 const bool has = base + lane < nsel;
                 const int i = has ? s_list[base + lane] : 0;
-                // Pass 1: Misra-Gries summary with three counters. The labels of
-                // the first kTileRows neighbours are staged into the tile with
-                // asynchronous copies (all in flight at once), then read from
-                // shared memory. Every label occurring more than deg / 4 times
-                // ends with a positive counter. Empty counters keep distinct
-                // negative labels until first filled; an empty counter that still
-                // holds x takes it back (the same summary as filling a free one,
-                // since no label is ever held by two counters).
-                int c0 = -1, c1 = -2, c2 = -3, n0 = 0, n1 = 0, n2 = 0;
-                auto mg = [&](int x, bool ok) {
-                    const bool m0 = x == c0, m1 = x == c1, m2 = x == c2;
-                    const bool hit = m0 || m1 || m2;
-                    const bool e0 = n0 == 0, e1 = n1 == 0, e2 = n2 == 0;
-                    const bool f0 = !hit && e0, f1 = !hit && !e0 && e1, f2 = !hit && !e0 && !e1 && e2;
-                    const int dec = (ok && !hit && !e0 && !e1 && !e2) ? 1 : 0;
-                    n0 = ok && (m0 || f0) ? n0 + 1 : n0 - dec;
-                    n1 = ok && (m1 || f1) ? n1 + 1 : n1 - dec;
-                    n2 = ok && (m2 || f2) ? n2 + 1 : n2 - dec;
-                    c0 = ok && f0 ? x : c0;
-                    c1 = ok && f1 ? x : c1;
-                    c2 = ok && f2 ? x : c2;
-                };
                 // The tile is read by the pass and by the votes of degree <= 32
                 // and > kDeferMax; pairs of the deferred degrees need it only
                 // for the pass. Degree <= kTileRows with enough selected pairs
@@ -858,40 +838,76 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                 }
                 cp_async_wait_all();
                 __syncwarp();
-                if (has && use_mg) {
-#pragma unroll 4
-                    for (int j = 0; j < dt; ++j) mg(tile[j * kTileStride + lane], true);
-                }
-                // Neighbours beyond the tile: global loads, eight in flight.
-                for (int e0 = kTileRows; use_mg && e0 < deg; e0 += 32) {
-                    const int my_u = e0 + lane < deg ? checked_node(__ldg(col_idx + beg + e0 + lane), gp.n) : 0;
-                    const int cnt = min(32, deg - e0);
-                    for (int j0 = 0; j0 < cnt; j0 += 8) {
-                        int xs[8];
-#pragma unroll
-                        for (int t = 0; t < 8; ++t) {
-                            const int u = __shfl_sync(kFull, my_u, min(j0 + t, cnt - 1));
-                            xs[t] = (has && j0 + t < cnt) ? child[(size_t)u * W + i] : 0;
+                // Pass 1: a Misra-Gries summary with K counters keeps every
+                // label occurring more than deg / (K + 1) times; pass 2 counts
+                // the survivors exactly. K = 1 (Boyer-Moore) up to degree
+                // 2 kTileRows, whose unsettled pairs take the cheap deferred
+                // vote; K = 3 above, where the fallback costs more and settling
+                // more pairs pays. The labels of the first kTileRows
+                // neighbours are read from the tile, the rest from global
+                // memory (eight loads in flight). Empty counters keep distinct
+                // negative labels until first filled; an empty counter that
+                // still holds x takes it back (the same summary as filling a
+                // free one, since no label is ever held by two counters).
+                const int kc = deg <= 2 * kTileRows ? 1 : 3;
+                int s0 = -2, s1 = -3, s2 = -4;  // candidates (labels no neighbour has when empty)
+                int h0 = 0, h1 = 0, h2 = 0;     // their exact counts
+                auto pass = [&](auto kconst) {
+                    constexpr int K = decltype(kconst)::value;
+                    int c0 = -1, c1 = -2, c2 = -3, n0 = 0, n1 = 0, n2 = 0;
+                    auto mg = [&](int x, bool ok) {
+                        if (K == 1) {
+                            const bool e0 = n0 == 0;
+                            n0 = !ok ? n0 : (x == c0 || e0) ? n0 + 1 : n0 - 1;
+                            c0 = ok && e0 ? x : c0;
+                            return;
                         }
-#pragma unroll
-                        for (int t = 0; t < 8; ++t) mg(xs[t], has && j0 + t < cnt);
-                    }
-                }
-                // Pass 2: exact counts of the surviving candidates.
-                // Live candidates; an empty counter gets a label no neighbour
-                // (nor the -1 padding below) can have, so it counts 0.
-                const int s0 = n0 > 0 ? c0 : -2, s1 = n1 > 0 ? c1 : -3, s2 = n2 > 0 ? c2 : -4;
-                int h0 = 0, h1 = 0, h2 = 0;
-                if (use_mg) {
-                    // The first kTileRows labels are still in the tile.
+                        const bool m0 = x == c0, m1 = x == c1, m2 = x == c2;
+                        const bool hit = m0 || m1 || m2;
+                        const bool e0 = n0 == 0, e1 = n1 == 0, e2 = n2 == 0;
+                        const bool f0 = !hit && e0, f1 = !hit && !e0 && e1, f2 = !hit && !e0 && !e1 && e2;
+                        const int dec = (ok && !hit && !e0 && !e1 && !e2) ? 1 : 0;
+                        n0 = ok && (m0 || f0) ? n0 + 1 : n0 - dec;
+                        n1 = ok && (m1 || f1) ? n1 + 1 : n1 - dec;
+                        n2 = ok && (m2 || f2) ? n2 + 1 : n2 - dec;
+                        c0 = ok && f0 ? x : c0;
+                        c1 = ok && f1 ? x : c1;
+                        c2 = ok && f2 ? x : c2;
+                    };
                     if (has) {
 #pragma unroll 4
-                        for (int j = 0; j < kTileRows; ++j) {
-                            const int x = tile[j * kTileStride + lane];
-                            h0 += x == s0;
+                        for (int j = 0; j < dt; ++j) mg(tile[j * kTileStride + lane], true);
+                    }
+                    for (int e0 = kTileRows; e0 < deg; e0 += 32) {
+                        const int my_u = e0 + lane < deg ? checked_node(__ldg(col_idx + beg + e0 + lane), gp.n) : 0;
+                        const int cnt = min(32, deg - e0);
+                        for (int j0 = 0; j0 < cnt; j0 += 8) {
+                            int xs[8];
+#pragma unroll
+                            for (int t = 0; t < 8; ++t) {
+                                const int u = __shfl_sync(kFull, my_u, min(j0 + t, cnt - 1));
+                                xs[t] = (has && j0 + t < cnt) ? child[(size_t)u * W + i] : 0;
+                            }
+#pragma unroll
+                            for (int t = 0; t < 8; ++t) mg(xs[t], has && j0 + t < cnt);
+                        }
+                    }
+                    s0 = n0 > 0 ? c0 : -2;
+                    if (K > 1) {
+                        s1 = n1 > 0 ? c1 : -3;
+                        s2 = n2 > 0 ? c2 : -4;
+                    }
+                    auto tally = [&](int x) {
+                        h0 += x == s0;
+                        if (K > 1) {
                             h1 += x == s1;
                             h2 += x == s2;
                         }
+                    };
+                    // The first kTileRows labels are still in the tile.
+                    if (has) {
+#pragma unroll 4
+                        for (int j = 0; j < kTileRows; ++j) tally(tile[j * kTileStride + lane]);
                     }
                     for (int e0 = kTileRows; e0 < deg; e0 += 32) {
                         const int my_u = e0 + lane < deg ? checked_node(__ldg(col_idx + beg + e0 + lane), gp.n) : 0;
@@ -904,18 +920,21 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
                                 xs[t] = (has && j0 + t < cnt) ? child[(size_t)u * W + i] : -1;
                             }
 #pragma unroll
-                            for (int t = 0; t < 8; ++t) {
-                                h0 += xs[t] == s0;
-                                h1 += xs[t] == s1;
-                                h2 += xs[t] == s2;
-                            }
+                            for (int t = 0; t < 8; ++t) tally(xs[t]);
                         }
                     }
+                };
+                if (use_mg) {
+                    if (kc == 1)
+                        pass(std::integral_constant<int, 1>{});
+                    else
+                        pass(std::integral_constant<int, 3>{});
                 }
-                // If the best candidate count c satisfies 4 c > deg, every label
-                // reaching c is a candidate: the tied set is complete and exact.
+                // If the best candidate count c satisfies (K + 1) c > deg, every
+                // label reaching c is a candidate: the tied set is complete and
+                // exact.
                 const int best = max(h0, max(h1, h2));
-                const bool done = has && use_mg && 4 * best > deg;
+                const bool done = has && use_mg && (kc + 1) * best > deg;
                 if (done) {
                     // Tied candidates in ascending order, then the MTIE pick.
                     int a = h0 == best ? s0 : INT_MAX;
@@ -1078,7 +1097,8 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
 // network, and the pick(u, t)-th of the t longest runs is the result, u the
 // MTIE word. The thread writes the label into Q, adds deg(v) to the degree
 // histogram (as the mutation kernel does for the other pairs) and, when the
-// best count c has 4 c > deg, counts the pair in v's hint.
+// best count c has (K + 1) c > deg (K the counters of the node's Misra-Gries
+// pass: 1 for degree <= 64, else 3), counts the pair in v's hint.
 template <int N>
 __global__ void __launch_bounds__(kMutBlock)
 mutation_vote_kernel(GenParams gp, int cls, const int32_t *__restrict__ row_ptr,
@@ -1172,7 +1192,7 @@ mutation_vote_kernel(GenParams gp, int cls, const int32_t *__restrict__ row_ptr,
         const int res = select_at<N>(x, pos);
         q[(size_t)v * W + i] = res;
         if (MOCD_CHECK(res >= 0 && res < gp.n, kCheckLabel, v)) atomicAdd(hist + (size_t)res * W + i, (unsigned)deg);
-        if (4 * best > deg) atomicAdd(hint + v, 1u);
+        if ((N <= 2 * kTileRows ? 2 : 4) * best > deg) atomicAdd(hint + v, 1u);
     }
 }
 
