@@ -394,11 +394,22 @@ int mocd_debug_inject(int32_t site, int32_t skip, int32_t count, int32_t status)
 int mocd_debug_checks(uint64_t *out, int32_t reset);
 
 /*
+ * Device memory: every device allocation of the library comes from one
+ * stream-ordered memory pool per device that the library creates. Memory a
+ * destroyed context (or finished server job) freed stays reserved in the
+ * pool for the next one, which then allocates without mapping fresh memory.
+ * mocd_pool_trim releases reserved memory of the current device's pool that
+ * is not in use, down to keep_bytes (0: all of it), e.g. before another part
+ * of the process needs the device memory. Errors: INVALID_ARG
+ * (keep_bytes < 0), CUDA.
+ */
+int mocd_pool_trim(int64_t keep_bytes);
+
+/*
  * Test support: bytes in use now and the high-water mark since the last
- * reset in the current device's default stream-ordered memory pool, from
- * which every device allocation of the library comes (reset_peak != 0 first
- * resets the mark to the current use). Either pointer may be NULL.
- * Errors: CUDA.
+ * reset in the current device's memory pool of the library (see
+ * mocd_pool_trim; reset_peak != 0 first resets the mark to the current use).
+ * Either pointer may be NULL. Errors: CUDA.
  */
 int mocd_debug_pool_usage(int32_t reset_peak, int64_t *current, int64_t *peak);
 

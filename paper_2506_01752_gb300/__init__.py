@@ -136,6 +136,7 @@ def load_library(path: str):
         "mocd_job_footprint": (ctypes.c_int, [i64, P, i32, P]),
         "mocd_debug_inject": (ctypes.c_int, [i32, i32, i32, i32]),
         "mocd_debug_pool_usage": (ctypes.c_int, [i32, P, P]),
+        "mocd_pool_trim": (ctypes.c_int, [i64]),
         "mocd_debug_checks": (ctypes.c_int, [P, i32]),
     }
     for name, (res, args) in sig.items():
@@ -457,6 +458,12 @@ def debug_pool_usage(reset_peak: bool = False):
     _check(load().mocd_debug_pool_usage(1 if reset_peak else 0, ctypes.byref(cur), ctypes.byref(peak)),
            "mocd_debug_pool_usage")
     return cur.value, peak.value
+
+
+def pool_trim(keep_bytes: int = 0) -> None:
+    """Release the device memory the library's pool keeps for later contexts
+    (down to keep_bytes)."""
+    _check(load().mocd_pool_trim(int(keep_bytes)), "mocd_pool_trim")
 
 
 def synchronize(ctx):

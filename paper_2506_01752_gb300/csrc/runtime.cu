@@ -12,11 +12,15 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
+#include <condition_variable>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <new>
 #include <thread>
 #include <vector>
+
+#include <unistd.h>
 
 #include "mocd.h"
 #include "mocd_internal.h"
@@ -108,9 +112,42 @@ int cuda_status(cudaError_t e)
         if (e_ != cudaSuccess) return cuda_status(e_);\
     } while (0)
 
-// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the
-// owner's stream): releasing one context never synchronises the device, so
-// other contexts (batch members, server jobs) keep running.
+// Device memory is stream-ordered (allocated and freed on the owner's
+// stream): releasing one context never synchronises the device, so other
+// contexts (batch members, server jobs) keep running. It comes from one
+// memory pool per device owned by the library, which keeps freed memory
+// for the next context instead of returning it to the driver at every
+// synchronisation (mapping fresh memory costs a job hundreds of
+// microseconds); mocd_pool_trim returns it.
+constexpr int kMaxDevices = 64;
+
+cudaError_t library_pool(int dev, cudaMemPool_t *out)
+{
+    static std::mutex mu;
+    static cudaMemPool_t pools[kMaxDevices] = {};
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        cudaError_t e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        unsigned long long keep = ~0ull;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        pools[dev] = pool;
+    }
+    *out = pools[dev];
+    return cudaSuccess;
+}
+
 void dev_free(void *p, cudaStream_t st)
 {
     if (p) cudaFreeAsync(p, st);
@@ -409,14 +446,111 @@ int validate_labels(const mocd_ctx *c, const int32_t *labels, size_t count)
     return MOCD_OK;
 }
 
-// Runs f(v0, v1) on contiguous node ranges of about equal edge counts, on up
-// to 16 threads (inline when the graph is small).
+// Host worker threads for the data-parallel host steps (graph validation,
+// mapping download pages). Created once per process on first use and kept:
+// a host step of a small job is shorter than creating and joining its
+// threads. run(T, f) calls f(t) for t in [0, T), chunk 0 on the calling
+// thread, and returns when all have finished. One step uses the workers at a
+// time; a call that finds them busy (another host thread of the caller, e.g.
+// a server admission thread) runs its chunks itself.
+class WorkerPool {
+  public:
+    static WorkerPool &get()
+    {
+        static std::mutex init_mu;
+        static WorkerPool *pool = nullptr;
+        static pid_t owner = 0;
+        std::lock_guard<std::mutex> lock(init_mu);
+        // A forked child has none of the parent's threads: it makes its own
+        // pool (the parent's object is left as it is).
+        if (!pool || owner != getpid()) {
+            const unsigned hw = std::thread::hardware_concurrency();
+            pool = new WorkerPool((int)std::min<unsigned>(hw ? hw : 1, 16) - 1);
+            owner = getpid();
+        }
+        return *pool;
+    }
+
+    int width() const { return (int)threads_.size() + 1; }
+
+    void run(int T, const std::function<void(int)> &f)
+    {
+        std::unique_lock<std::mutex> busy(run_mu_, std::try_to_lock);
+        if (T <= 1 || threads_.empty() || !busy.owns_lock()) {
+            for (int t = 0; t < T; ++t) f(t);
+            return;
+        }
+        {
+            std::lock_guard<std::mutex> lock(mu_);
+            job_ = &f;
+            chunks_ = T;
+            next_ = 1;
+            pending_ = T - 1;
+            ++epoch_;
+        }
+        cv_work_.notify_all();
+        f(0);
+        for (;;) {  // the caller takes chunks too
+            int t;
+            {
+                std::lock_guard<std::mutex> lock(mu_);
+                if (next_ >= chunks_) break;
+                t = next_++;
+            }
+            f(t);
+            std::lock_guard<std::mutex> lock(mu_);
+            --pending_;
+        }
+        std::unique_lock<std::mutex> lock(mu_);
+        cv_done_.wait(lock, [&] { return pending_ == 0; });
+        job_ = nullptr;
+    }
+
+  private:
+    explicit WorkerPool(int workers)
+    {
+        for (int k = 0; k < workers; ++k) {
+            std::thread th([this] { loop(); });
+            th.detach();  // the pool lives until the process ends
+            threads_.push_back(std::move(th));
+        }
+    }
+
+    void loop()
+    {
+        uint64_t seen = 0;
+        std::unique_lock<std::mutex> lock(mu_);
+        for (;;) {
+            cv_work_.wait(lock, [&] { return epoch_ != seen && next_ < chunks_; });
+            seen = epoch_;
+            while (next_ < chunks_) {
+                const int t = next_++;
+                const std::function<void(int)> *f = job_;
+                lock.unlock();
+                (*f)(t);
+                lock.lock();
+                if (--pending_ == 0) cv_done_.notify_all();
+            }
+        }
+    }
+
+    std::mutex run_mu_;  // one host step at a time
+    std::mutex mu_;
+    std::condition_variable cv_work_, cv_done_;
+    std::vector<std::thread> threads_;
+    const std::function<void(int)> *job_ = nullptr;
+    int chunks_ = 0, next_ = 0, pending_ = 0;
+    uint64_t epoch_ = 0;
+};
+
+// Runs f(v0, v1) on contiguous node ranges of about equal edge counts, on the
+// worker pool (inline when the graph is small).
 template <class F>
 void parallel_rows(const int64_t *row_ptr, int64_t n, F f)
 {
     const int64_t nnz = row_ptr[n];
-    const unsigned hw = std::thread::hardware_concurrency();
-    int64_t T = std::min<int64_t>(std::min<int64_t>(hw ? hw : 1, 16), (nnz + n) / (1 << 16) + 1);
+    WorkerPool &pool = WorkerPool::get();
+    const int64_t T = std::min<int64_t>(pool.width(), (nnz + n) / (1 << 15) + 1);
     if (T <= 1) {
         f(0, n);
         return;
@@ -426,30 +560,23 @@ void parallel_rows(const int64_t *row_ptr, int64_t n, F f)
     cut[(size_t)T] = n;
     for (int64_t t = 1; t < T; ++t)
         cut[(size_t)t] = std::lower_bound(row_ptr, row_ptr + n, nnz * t / T) - row_ptr;
-    std::vector<std::thread> th;
-    th.reserve((size_t)T - 1);
-    for (int64_t t = 1; t < T; ++t) th.emplace_back(f, cut[(size_t)t], cut[(size_t)t + 1]);
-    f(cut[0], cut[1]);
-    for (auto &x : th) x.join();
+    pool.run((int)T, [&](int t) { f(cut[(size_t)t], cut[(size_t)t + 1]); });
 }
 
-// Writes one zero per 4 KiB of [p, p + bytes) from up to 16 threads: maps
-// every page of a buffer that is about to be overwritten.
+// Writes one zero per 4 KiB of [p, p + bytes) on the worker pool: maps every
+// page of a buffer that is about to be overwritten, so that the copy into it
+// does not fault page by page.
 void prefault(void *p, size_t bytes)
 {
     constexpr size_t kPage = 4096;
     const size_t pages = bytes / kPage;
     if (pages < 256) return;
     volatile char *base = static_cast<volatile char *>(p);
-    const unsigned hw = std::thread::hardware_concurrency();
-    const size_t T = std::min<size_t>(std::min<size_t>(hw ? hw : 1, 16), pages / 256);
-    auto touch = [&](size_t a, size_t b) {
-        for (size_t k = a; k < b; ++k) base[k * kPage] = 0;
-    };
-    std::vector<std::thread> th;
-    for (size_t t = 1; t < T; ++t) th.emplace_back(touch, pages * t / T, pages * (t + 1) / T);
-    touch(0, pages / T);
-    for (auto &x : th) x.join();
+    WorkerPool &pool = WorkerPool::get();
+    const size_t T = std::min<size_t>((size_t)pool.width(), pages / 256);
+    pool.run((int)T, [&](int t) {
+        for (size_t k = pages * (size_t)t / T; k < pages * ((size_t)t + 1) / T; ++k) base[k * kPage] = 0;
+    });
 }
 
 // The status of the lowest-numbered failing row among concurrent checks.
@@ -650,7 +777,15 @@ cudaError_t mocd::dev_alloc(void **p, size_t bytes, cudaStream_t st)
         *p = nullptr;
         return cudaErrorMemoryAllocation;
     }
-    return cudaMallocAsync(p, bytes, st);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    cudaMemPool_t pool = nullptr;
+    if (e == cudaSuccess) e = library_pool(dev, &pool);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return e;
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, st);
 }
 
 int mocd::record_on_stream(mocd_ctx *c, cudaEvent_t ev)
@@ -688,55 +823,61 @@ int mocd_graph_upload(mocd_ctx **out, int64_t n, const int64_t *row_ptr, const i
     *out = nullptr;
     if (!row_ptr || n < 1 || n >= (int64_t(1) << 30)) return MOCD_ERR_INVALID_ARG;
     if (row_ptr[0] != 0) return MOCD_ERR_INVALID_ARG;
-    for (int64_t v = 0; v < n; ++v)
+    int dmax = 0;
+    for (int64_t v = 0; v < n; ++v) {
         if (row_ptr[v + 1] < row_ptr[v]) return MOCD_ERR_INVALID_ARG;
+        dmax = (int)std::min<int64_t>(std::max<int64_t>(dmax, row_ptr[v + 1] - row_ptr[v]), INT_MAX);
+    }
     const int64_t nnz = row_ptr[n];
     if (nnz >= (int64_t(1) << 31)) return MOCD_ERR_INVALID_ARG;
     if (nnz > 0 && !col_idx) return MOCD_ERR_INVALID_ARG;
-    // Rows that are already strictly increasing are used as given; otherwise
-    // a sorted copy of the adjacency is made. Then per row (in sorted order):
-    // range, self loop, repeat; then symmetry. The first failing row decides
-    // the status, as a sequential scan would.
-    std::atomic<bool> all_increasing{true};
-    parallel_rows(row_ptr, n, [&](int64_t v0, int64_t v1) {
-        for (int64_t v = v0; v < v1 && all_increasing.load(std::memory_order_relaxed); ++v)
-            for (int64_t k = row_ptr[v] + 1; k < row_ptr[v + 1]; ++k)
-                if (col_idx[k] <= col_idx[k - 1]) {
-                    all_increasing.store(false, std::memory_order_relaxed);
-                    break;
+    // Per row, in sorted order: range, self loop, repeat; then symmetry. The
+    // first failing row decides the status, as a sequential scan would. One
+    // pass checks the rows as given and whether each is strictly increasing;
+    // if one is not, a sorted copy of the adjacency is made and checked again
+    // (the order of the entries decides which failure a row reports).
+    auto check_rows = [&](const int32_t *adj_rows, std::atomic<bool> *increasing) {
+        FirstError err;
+        parallel_rows(row_ptr, n, [&](int64_t v0, int64_t v1) {
+            for (int64_t v = v0; v < v1; ++v) {
+                const int32_t *b = adj_rows + row_ptr[v], *e = adj_rows + row_ptr[v + 1];
+                for (const int32_t *q = b; q < e; ++q) {
+                    if (increasing && q > b && q[-1] > *q) increasing->store(false, std::memory_order_relaxed);
+                    int rc = MOCD_OK;
+                    if (*q < 0 || *q >= n) rc = MOCD_ERR_INVALID_ARG;
+                    else if (*q == v) rc = MOCD_ERR_SELF_LOOP;
+                    else if (q > b && q[-1] == *q) rc = MOCD_ERR_DUPLICATE_EDGE;
+                    if (rc) {
+                        // The row's failure is the one its sorted order shows
+                        // first: if the row is not sorted, the sorted copy
+                        // decides (the rows before it in this range were
+                        // scanned in full).
+                        for (const int32_t *r = q + 1; increasing && r < e; ++r)
+                            if (r[-1] > *r) increasing->store(false, std::memory_order_relaxed);
+                        err.record(v, rc);
+                        return;
+                    }
                 }
-    });
+            }
+        });
+        return err.status();
+    };
+    std::atomic<bool> all_increasing{true};
     std::vector<int32_t> adj;
     const int32_t *src = col_idx;
+    int status = check_rows(col_idx, &all_increasing);
     if (!all_increasing.load()) {
         adj.assign(col_idx, col_idx + nnz);
         parallel_rows(row_ptr, n, [&](int64_t v0, int64_t v1) {
             for (int64_t v = v0; v < v1; ++v) std::sort(adj.data() + row_ptr[v], adj.data() + row_ptr[v + 1]);
         });
         src = adj.data();
+        status = check_rows(src, nullptr);
     }
-    FirstError err;
-    parallel_rows(row_ptr, n, [&](int64_t v0, int64_t v1) {
-        for (int64_t v = v0; v < v1; ++v) {
-            const int32_t *b = src + row_ptr[v], *e = src + row_ptr[v + 1];
-            for (const int32_t *q = b; q < e; ++q) {
-                int rc = MOCD_OK;
-                if (*q < 0 || *q >= n) rc = MOCD_ERR_INVALID_ARG;
-                else if (*q == v) rc = MOCD_ERR_SELF_LOOP;
-                else if (q > b && q[-1] == *q) rc = MOCD_ERR_DUPLICATE_EDGE;
-                if (rc) {
-                    err.record(v, rc);
-                    return;
-                }
-            }
-        }
-    });
-    if (err.status()) return err.status();
+    if (status) return status;
     // Symmetry is checked on the device once the CSR is there (below): a
     // binary search per stored entry, which the host's scattered memory
     // accesses make slow for large graphs.
-    int dmax = 0;
-    for (int64_t v = 0; v < n; ++v) dmax = std::max<int>(dmax, (int)(row_ptr[v + 1] - row_ptr[v]));
     if (nnz == 0) return MOCD_ERR_EMPTY_GRAPH;
 
     mocd_ctx *c = new (std::nothrow) mocd_ctx();
@@ -1342,12 +1483,23 @@ int mocd_debug_checks(uint64_t *out, int32_t reset)
 #endif
 }
 
+int mocd_pool_trim(int64_t keep_bytes)
+{
+    if (keep_bytes < 0) return MOCD_ERR_INVALID_ARG;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    cudaMemPool_t pool = nullptr;
+    CK(library_pool(dev, &pool));
+    CK(cudaMemPoolTrimTo(pool, (size_t)keep_bytes));
+    return MOCD_OK;
+}
+
 int mocd_debug_pool_usage(int32_t reset_peak, int64_t *current, int64_t *peak)
 {
     int dev = 0;
     CK(cudaGetDevice(&dev));
     cudaMemPool_t pool = nullptr;
-    CK(cudaDeviceGetDefaultMemPool(&pool, dev));
+    CK(library_pool(dev, &pool));
     if (reset_peak) {
         unsigned long long zero = 0;
         CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
@@ -1377,7 +1529,6 @@ void mocd_destroy(mocd_ctx *c)
     dev_free(c->d_volsize, c->stream);
     dev_free(c->d_cut, c->stream);
     dev_free(c->d_stats, c->stream);
-    if (c->stream) cudaStreamSynchronize(c->stream);
     for (int k = 0; k <= kStages; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

@@ -110,7 +110,8 @@ def test_large_graph_validation_passes_with_shuffled_rows(lib):
     assert _upload_status(rp, ci) not in _validation_codes()
 
 
-@pytest.mark.parametrize("defect", ["self_loop_first", "range_first", "dup_unsorted"])
+@pytest.mark.parametrize("defect", ["self_loop_first", "range_first", "dup_unsorted", "sorted_order_decides",
+                                    "hidden_repeat"])
 def test_large_graph_first_failing_row_decides(lib, defect):
     """Defects in rows handled by different threads: the status is that of
     the lowest-numbered failing row, as in a sequential scan. (Symmetry is
@@ -125,10 +126,29 @@ def test_large_graph_first_failing_row_decides(lib, defect):
         ci[rp[lo]] = -7
         ci[rp[hi]] = hi
         want = -1
-    else:
+    elif defect == "dup_unsorted":
         seg = ci[rp[hi]:rp[hi + 1]].copy()
         seg[-1] = seg[0]           # repeated neighbour
         ci[rp[hi]:rp[hi + 1]] = seg[::-1]
+        want = -4
+    elif defect == "sorted_order_decides":
+        # Row lo as given meets a repeat before an out-of-range id; in sorted
+        # order the negative id comes first, so the row fails as out of range.
+        v = next(u for u in range(lo, hi) if rp[u + 1] - rp[u] >= 4)
+        a = ci[rp[v]]
+        b = ci[rp[v] + 1]
+        ci[rp[v]:rp[v] + 4] = [a, b, b, -1]
+        ci[rp[hi]] = hi            # a later row with a self loop
+        want = -1
+    else:
+        # Row lo repeats a neighbour non-adjacently (unsorted): only the
+        # sorted order shows the repeat.
+        v = next(u for u in range(lo, hi) if rp[u + 1] - rp[u] >= 3)
+        seg = ci[rp[v]:rp[v + 1]].copy()
+        seg[2] = seg[0]
+        seg[0], seg[1] = seg[1], seg[0]
+        ci[rp[v]:rp[v + 1]] = seg
+        ci[rp[hi]] = -3            # a later row out of range
         want = -4
     assert _upload_status(rp, ci) == want
 

@@ -127,3 +127,36 @@ def test_job_footprint_bounds_the_pool_peak(pop):
     fp = mocd.job_footprint(rp, pop)
     assert 0 < peak - cur0 <= fp + 16 * (2 << 20), (peak - cur0, fp)
     assert peak - cur0 >= 0.8 * fp, (peak - cur0, fp)  # and the estimate is not loose
+
+
+def test_pool_keeps_freed_memory_until_trimmed():
+    """A destroyed context's memory stays reserved in the library's pool (the
+    next context reuses it without mapping fresh memory); mocd_pool_trim
+    gives it back to the device."""
+    torch = pytest.importorskip("torch")
+    rp, ci = synth.lfr_style(100_000, 16, 60, 0.3, seed=9)[:2]
+    fp = mocd.job_footprint(rp, 100)
+    h = mocd.graph_upload(rp, ci)
+    try:
+        mocd.population_init(h, mocd.Params())
+        mocd.generation(h, 1)
+        mocd.synchronize(h)
+    finally:
+        mocd.destroy(h)
+    torch.cuda.synchronize()
+    cur, _ = mocd.debug_pool_usage()
+    held = torch.cuda.mem_get_info()[0]
+    mocd.pool_trim(0)
+    freed = torch.cuda.mem_get_info()[0] - held
+    assert freed >= 0.5 * fp, (freed, fp)
+    assert mocd.debug_pool_usage()[0] == cur  # trimming releases only unused memory
+    # and the pool serves the next context as before
+    h = mocd.graph_upload(rp, ci)
+    try:
+        mocd.population_init(h, mocd.Params())
+        mocd.generation(h, 1)
+        mocd.synchronize(h)
+    finally:
+        mocd.destroy(h)
+    with pytest.raises(mocd.MocdError):
+        mocd.pool_trim(-1)
