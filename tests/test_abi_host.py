@@ -159,3 +159,36 @@ def test_debug_build_loads_and_exports_every_symbol():
     lib = mocd.load_library(cuda_build.build(debug=True))
     for name in declared_functions():
         assert hasattr(lib, name), name
+
+
+def test_concurrent_validation_from_several_threads(lib):
+    """Host threads validating graphs at the same time (as the server's
+    admission threads do) share the library's worker threads or run their
+    checks themselves; every call still reports its own graph's status."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    rp, ci = _big_graph()
+    cases = []
+    for k in range(12):
+        c = ci.copy()
+        if k % 3 == 0:
+            c[rp[10 + k]] = 10 + k  # self loop
+            want = -3
+        elif k % 3 == 1:
+            c[rp[500 + k]] = -1     # out of range
+            want = -1
+        else:
+            want = None             # valid: fails later, at the device step, without a GPU
+        cases.append((c, want))
+
+    def upload(case):
+        c, want = case
+        return _upload_status(rp, c), want
+
+    with ThreadPoolExecutor(max_workers=6) as ex:
+        for _ in range(3):
+            for got, want in ex.map(upload, cases):
+                if want is None:
+                    assert got not in _validation_codes()
+                else:
+                    assert got == want
