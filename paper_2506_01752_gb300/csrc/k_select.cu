@@ -49,6 +49,7 @@ struct SelShared {
     unsigned long long sa[kMaxPoints], sb[kMaxPoints];
     int ia[kMaxPoints], ib[kMaxPoints];
     unsigned long long wscan[kSelWarps];
+    int wscan2[kSelWarps];
     int fsize[kMaxPoints + 1];
     int keep[kMaxPop];
     unsigned long long xa[2][kMaxPoints], xb[2][kMaxPoints];  // sort exchange, double-buffered
@@ -145,6 +146,34 @@ __device__ int block_max_scan(SelShared &S, int v)
     for (int q = 0; q < kSelWarps; ++q) pre = q < w ? max(pre, (int)(unsigned)S.wscan[q]) : pre;
     __syncthreads();
     return max(v, pre);
+}
+
+// In one pass over the block: a forward inclusive max-scan of two 16-bit
+// values packed in a (per half-word) and a backward inclusive min-scan of b
+// (over threads t .. kSelThreads - 1).
+__device__ void block_scan_pair(SelShared &S, unsigned &a, int &b)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned ya = __shfl_up_sync(kFull, a, d);
+        const int yb = __shfl_down_sync(kFull, b, d);
+        if (lane >= d) a = __vmaxu2(a, ya);
+        if (lane + d < 32) b = min(b, yb);
+    }
+    if (lane == 31) S.wscan[w] = a;
+    if (lane == 0) S.wscan2[w] = b;
+    __syncthreads();
+    unsigned pa = 0;
+    int pb = INT_MAX;
+#pragma unroll
+    for (int q = 0; q < kSelWarps; ++q) {
+        pa = q < w ? __vmaxu2(pa, (unsigned)S.wscan[q]) : pa;
+        pb = q > w ? min(pb, S.wscan2[q]) : pb;
+    }
+    __syncthreads();
+    a = __vmaxu2(a, pa);
+    b = min(b, pb);
 }
 
 // rank[], crowd[] and order[] of the first N points of S.k1 / S.k2 (N <= 256),
@@ -249,23 +278,17 @@ __device__ void rank_crowd_order(SelShared &S, int N, bool known_rank)
     S.sb[t] = (unsigned long long)e2;
     S.ib[t] = er;
     __syncthreads();
+    // Start of t's front and of its group of identical points (forward max
+    // scans of the head positions), and the end of its group (the next group
+    // head after t: a backward min scan), all in one pass.
     const bool fhead = t == 0 || S.ib[t - 1] != er;
-    const int fstart = block_max_scan(S, fhead ? t : 0);
     const bool ghead = fhead || S.sa[t - 1] != (unsigned long long)e1 || S.sb[t - 1] != (unsigned long long)e2;
-    const int gs = block_max_scan(S, ghead ? t : 0);
-    // End of t's group: the next group head at or after t + 1, via a min scan
-    // over the reversed order.
-    {
-        const int rt = kSelThreads - 1 - t;
-        const bool rhead = rt == kSelThreads - 1 ? true
-                                                 : (S.ib[rt + 1] != S.ib[rt] || S.sa[rt + 1] != S.sa[rt] ||
-                                                    S.sb[rt + 1] != S.sb[rt]);
-        // rhead: position rt + 1 starts a new group (or rt is the last slot)
-        const unsigned long long nh = block_min_scan(S, rhead ? (unsigned long long)(rt + 1) : kInf64);
-        S.ia[rt] = (int)nh;  // first group head after rt
-    }
-    __syncthreads();
-    const int ge = S.ia[t];
+    const bool gnext = t == kSelThreads - 1 || S.ib[t + 1] != er || S.sa[t + 1] != (unsigned long long)e1 ||
+                       S.sb[t + 1] != (unsigned long long)e2;
+    unsigned heads = ((fhead ? (unsigned)t : 0u) << 16) | (ghead ? (unsigned)t : 0u);
+    int ge = gnext ? t + 1 : INT_MAX;
+    block_scan_pair(S, heads, ge);
+    const int fstart = (int)(heads >> 16), gs = (int)(heads & 0xffffu);
     if (ereal) {
         const int F = S.fsize[er];
         const int fpos = t - fstart, gsl = gs - fstart, gel = ge - fstart;
