@@ -192,3 +192,32 @@ def test_concurrent_validation_from_several_threads(lib):
                     assert got not in _validation_codes()
                 else:
                     assert got == want
+
+
+def _validate_in_child(conn):
+    rp, ci = _big_graph()
+    c = ci.copy()
+    c[rp[123]] = 123  # self loop
+    conn.send(_upload_status(rp, c))
+    conn.close()
+
+
+@pytest.mark.filterwarnings("ignore::DeprecationWarning")  # forking a threaded process is the point
+def test_validation_in_a_forked_child(lib):
+    """A process forked after the library's worker threads exist (they do not
+    survive the fork) makes its own: validation in the child completes."""
+    import multiprocessing as mp
+
+    rp, ci = _big_graph()
+    assert _upload_status(rp, ci) not in _validation_codes()  # the parent's workers exist now
+    ctx = mp.get_context("fork")
+    parent, child = ctx.Pipe()
+    p = ctx.Process(target=_validate_in_child, args=(child,))
+    p.start()
+    try:
+        assert parent.poll(120), "validation in the forked child did not finish"
+        assert parent.recv() == -3
+    finally:
+        p.join(30)
+        if p.is_alive():
+            p.kill()
