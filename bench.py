@@ -308,6 +308,28 @@ def cpu_oracle_sample(rp, ci, seed: int, budget_s: float = 12.0, max_gens: int =
                       f"single-threaded C oracle, {dt:.1f} s", **cpu_description()}
 
 
+def cpu_oracle_sample_all_cores(rp, ci, seed: int, budget_s: float = 6.0, max_gens: int = 20):
+    """The oracle's threaded form (each generation's children split over all
+    host cores; the same sequential code per child, so the same result) for
+    whole generations of the same workload until the budget is spent."""
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    params = oracle.Params(seed=seed)
+    st = oracle.population_init(rp, ci, params)
+    m = int(rp[-1] // 2)
+    gens, t0 = 0, time.perf_counter()
+    while gens < max_gens:
+        st = oracle.run_parallel(rp, ci, params, st, 1, threads)
+        gens += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": params.pop_size * m * gens / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{gens} whole generations (N_p={params.pop_size}) of the same workload, children of "
+                      f"each generation over {threads} host threads, {dt:.1f} s", **cpu_description()}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -524,9 +546,10 @@ def run_mine(args):
     large = None
     if world == 1 and args.large != "none":
         large = large_leg(args, dev, stream, peak, peak_kind)
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(rp, ci, args.seed)
+        cpu_all = cpu_oracle_sample_all_cores(rp, ci, args.seed)
 
     if rank == 0:
         line = {
@@ -544,6 +567,7 @@ def run_mine(args):
             "roofline_objective": roofline_objective,
             "roofline_hbm": large,
             "cpu_baseline": cpu,
+            "cpu_baseline_all_cores": cpu_all,
             "e2e": e2e,
             "gpu_launches": kernels_per_generation * args.steps,
             "clocks": clocks,
