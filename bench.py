@@ -579,6 +579,10 @@ def run_mine(args):
     return 0
 
 
+FORMS = {0: "per-member kernel chains", 1: "per-member chains, one merged selection launch",
+         2: "one launch per stage for all members (mutation kernels per member)"}
+
+
 def run_batch(args):
     """64 uneven jobs (synth.batch_instances): one batched CUDA-graph launch
     per generation of all of them, against the plain path that runs one
@@ -605,11 +609,11 @@ def run_batch(args):
     init_all()
     b = mocd.batch_create(ctxs, stream)
     shape = mocd.batch_autotune(b, 2)
-    _, merged = mocd.batch_form(b)
+    _, form = mocd.batch_form(b)
     mocd.batch_destroy(b)
     init_all()
     b = mocd.batch_create(ctxs, stream)
-    mocd.batch_configure(b, shape, merged)
+    mocd.batch_configure(b, shape, form)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
 
@@ -633,16 +637,20 @@ def run_batch(args):
     batch_ms = timed(lambda: mocd.batch_generation(b, 1))
     mocd.batch_synchronize(b)
     mocd.batch_destroy(b)
-    # The other selection form at the same shape, for comparison (the same
-    # generations of fresh populations).
-    init_all()
-    b = mocd.batch_create(ctxs, stream)
-    mocd.batch_configure(b, shape, not merged)
-    mocd.batch_generation(b, args.warmup)
-    mocd.batch_synchronize(b)
-    other_ms = timed(lambda: mocd.batch_generation(b, 1))
-    mocd.batch_synchronize(b)
-    mocd.batch_destroy(b)
+    # The other forms at the same shape, for comparison (the same generations
+    # of fresh populations).
+    other_ms = {}
+    for other in (0, 1, 2):
+        if other == form:
+            continue
+        init_all()
+        b = mocd.batch_create(ctxs, stream)
+        mocd.batch_configure(b, shape, other)
+        mocd.batch_generation(b, args.warmup)
+        mocd.batch_synchronize(b)
+        other_ms[other] = statistics.fmean(timed(lambda: mocd.batch_generation(b, 1)))
+        mocd.batch_synchronize(b)
+        mocd.batch_destroy(b)
 
     # Plain path: each instance's own generation graph, one instance at a time.
     init_all()
@@ -680,8 +688,8 @@ def run_batch(args):
     line = {
         "metric": METRIC + " [batched jobs]", "value": units / (bt / 1e3), "unit": UNIT,
         "value_plain": units / (pt / 1e3), "speedup_vs_plain": pt / bt,
-        "selection_form": "merged (one launch for all members)" if merged else "per member",
-        "ms_per_step_other_form": statistics.fmean(other_ms),
+        "form": FORMS[form],
+        "ms_per_step_other_forms": {FORMS[k]: v for k, v in other_ms.items()},
         "ms_per_step": bt, "ms_per_step_plain": pt, "steps": args.steps, "warmup": args.warmup,
         "job_latency_ms": {"batched_p50": float(np.percentile(batch_lat, 50)),
                            "batched_p99": float(np.percentile(batch_lat, 99)),

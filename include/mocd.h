@@ -267,29 +267,34 @@ int mocd_evaluate_noalloc(const int32_t *row_ptr, const int32_t *col_idx, int64_
  *                       a member invalidates the batch (NOT_READY).
  *   mocd_batch_autotune picks the launch shape (nodes per warp of the node
  *                       kernels, one of 1, 2, 4, 8, 16) with the shortest
- *                       measured batch generation, then the selection form
- *                       at that shape (below); each trial runs
+ *                       measured batch generation, then the form at that
+ *                       shape (below); each trial runs
  *                       `generations_per_trial` generations, so the
  *                       populations advance (re-initialise afterwards for a
  *                       run from generation 0). Results never depend on the
  *                       launch shape or form. Writes the shape to
  *                       *nodes_per_warp.
  *   mocd_batch_configure sets the form explicitly: the nodes per warp (1, 2,
- *                       4, 8 or 16) and merged_select: 0 runs each member's
- *                       environmental selection at the end of its own kernel
- *                       chain (the chains proceed independently), 1 runs the
- *                       selections of all members in one launch (a block per
- *                       member) after every chain has evaluated.
+ *                       4, 8 or 16) and form: 0 runs each member's whole
+ *                       kernel chain, environmental selection included, on
+ *                       its own graph branch (the chains proceed
+ *                       independently); 1 runs the selections of all members
+ *                       in one launch (a block per member) after every chain
+ *                       has evaluated; 2 also runs the crossover, the
+ *                       deferred per-pair mutation votes and the evaluation
+ *                       of all members in one launch each (each member owns a
+ *                       range of the launch's blocks), only the mutation
+ *                       kernels staying per member.
  *                       Errors: INVALID_ARG, NOT_READY, CUDA.
- *   mocd_batch_form     reports the current nodes per warp and selection form.
+ *   mocd_batch_form     reports the current nodes per warp and form.
  */
 typedef struct mocd_batch mocd_batch;
 int mocd_batch_create(mocd_batch **out, int32_t count, mocd_ctx *const *ctxs, void *cuda_stream);
 int mocd_batch_generation(mocd_batch *b, int32_t n_generations);
 int mocd_batch_autotune(mocd_batch *b, int32_t generations_per_trial, int32_t *nodes_per_warp);
 int mocd_batch_synchronize(mocd_batch *b);
-int mocd_batch_configure(mocd_batch *b, int32_t nodes_per_warp, int32_t merged_select);
-int mocd_batch_form(mocd_batch *b, int32_t *nodes_per_warp, int32_t *merged_select);
+int mocd_batch_configure(mocd_batch *b, int32_t nodes_per_warp, int32_t form);
+int mocd_batch_form(mocd_batch *b, int32_t *nodes_per_warp, int32_t *form);
 void mocd_batch_destroy(mocd_batch *b);
 
 /*

@@ -335,17 +335,19 @@ def batch_autotune(b, generations_per_trial: int = 3) -> int:
     return out.value
 
 
-def batch_configure(b, nodes_per_warp: int = 1, merged_select: bool = False):
-    """Launch shape and selection form of a batch (see mocd_batch_configure)."""
-    _check(load().mocd_batch_configure(b, int(nodes_per_warp), 1 if merged_select else 0), "mocd_batch_configure")
+def batch_configure(b, nodes_per_warp: int = 1, form: int = 0):
+    """Launch shape and form of a batch (see mocd_batch_configure): form 0 per
+    member, 1 merged selection, 2 merged crossover, votes, evaluation and
+    selection."""
+    _check(load().mocd_batch_configure(b, int(nodes_per_warp), int(form)), "mocd_batch_configure")
 
 
 def batch_form(b):
-    """(nodes per warp, merged selection) of a batch."""
+    """(nodes per warp, form) of a batch."""
     npw = ctypes.c_int32()
-    merged = ctypes.c_int32()
-    _check(load().mocd_batch_form(b, ctypes.byref(npw), ctypes.byref(merged)), "mocd_batch_form")
-    return npw.value, bool(merged.value)
+    form = ctypes.c_int32()
+    _check(load().mocd_batch_form(b, ctypes.byref(npw), ctypes.byref(form)), "mocd_batch_form")
+    return npw.value, form.value
 
 
 def batch_synchronize(b):

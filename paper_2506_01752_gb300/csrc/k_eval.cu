@@ -41,11 +41,11 @@ namespace mocd {
 namespace {
 
 template <bool LABEL_MAJOR, bool COUNT_D>
-__global__ void __launch_bounds__(kBlock)
-evaluate_kernel(int n, int W, int count, const int32_t *__restrict__ row_ptr,
-                const int32_t *__restrict__ col_idx, const int32_t *__restrict__ labels,
-                uint32_t *__restrict__ hist, unsigned long long *__restrict__ acc,
-                const int32_t *__restrict__ order)
+__device__ __forceinline__ void evaluate_body(int n, int W, int count, const int32_t *__restrict__ row_ptr,
+                                              const int32_t *__restrict__ col_idx,
+                                              const int32_t *__restrict__ labels, uint32_t *__restrict__ hist,
+                                              unsigned long long *__restrict__ acc,
+                                              const int32_t *__restrict__ order, int vblock, int vgrid)
 {
     __shared__ unsigned long long s_intra[kMaxPop];
     __shared__ unsigned long long s_sq[kMaxPop];
@@ -59,8 +59,8 @@ evaluate_kernel(int n, int W, int count, const int32_t *__restrict__ row_ptr,
     const int lane = threadIdx.x & 31;
     const int nq = W >> 2;
     const bool active = lane < nq;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int warp = (vblock * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (vgrid * blockDim.x) >> 5;
     const int4 *__restrict__ L4 = reinterpret_cast<const int4 *>(labels);
     const int i0 = 4 * lane;
     int *nb = s_nb + (threadIdx.x & ~31);
@@ -167,6 +167,35 @@ evaluate_kernel(int n, int W, int count, const int32_t *__restrict__ row_ptr,
     }
 }
 
+template <bool LABEL_MAJOR, bool COUNT_D>
+__global__ void __launch_bounds__(kBlock)
+evaluate_kernel(int n, int W, int count, const int32_t *__restrict__ row_ptr,
+                const int32_t *__restrict__ col_idx, const int32_t *__restrict__ labels,
+                uint32_t *__restrict__ hist, unsigned long long *__restrict__ acc,
+                const int32_t *__restrict__ order)
+{
+    evaluate_body<LABEL_MAJOR, COUNT_D>(n, W, count, row_ptr, col_idx, labels, hist, acc, order, blockIdx.x,
+                                        gridDim.x);
+}
+
+// The offspring evaluation of every member of a batch in one launch: members
+// own consecutive block ranges (starts[k] .. starts[k + 1] - 1).
+__global__ void __launch_bounds__(kBlock, 4)
+evaluate_multi_kernel(const BatchMember *__restrict__ members, const int *__restrict__ starts, int count)
+{
+    const int bk = (int)blockIdx.x;
+    int lo = 0, hi = count;  // starts[lo] <= bk < starts[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(starts + mid) <= bk) lo = mid;
+        else hi = mid;
+    }
+    const BatchMember &mb = members[lo];
+    const int b0 = __ldg(starts + lo);
+    evaluate_body<true, false>(mb.gp.n, mb.gp.W, mb.gp.np, mb.row_ptr, mb.col_idx, mb.ps.q, mb.ps.hist, mb.ps.acc,
+                               mb.order, bk - b0, __ldg(starts + lo + 1) - b0);
+}
+
 }  // namespace
 
 int grid_for_eval(int sms, bool label_major)
@@ -198,6 +227,13 @@ cudaError_t launch_evaluate(int n, int W, int count, const int32_t *row_ptr, con
     else
         evaluate_kernel<false, true><<<grid, kBlock, 0, s>>>(n, W, count, row_ptr, col_idx, labels, hist, acc,
                                                              order);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_evaluate_multi(const BatchMember *members, const int *starts, int count, int blocks,
+                                  cudaStream_t s)
+{
+    if (blocks > 0) evaluate_multi_kernel<<<blocks, kBlock, 0, s>>>(members, starts, count);
     return cudaGetLastError();
 }
 

@@ -157,15 +157,15 @@ __device__ __forceinline__ int kth_tied(const int (&x)[EMAX], int E, int best, i
 }
 
 template <int EMAX>
-__global__ void __launch_bounds__(kBlock)
-crossover_kernel(GenParams gp, const int32_t *buf0, const int32_t *buf1, int32_t *out0, int32_t *out1,
-                 const int32_t *__restrict__ q, int32_t *__restrict__ child,
-                 const int32_t *__restrict__ keep, const int32_t *__restrict__ par_r,
-                 const int32_t *__restrict__ copy_r, const uint32_t *__restrict__ gen_ptr,
-                 int *__restrict__ dcount)
+__device__ __forceinline__ void crossover_body(const GenParams &gp, const int32_t *buf0, const int32_t *buf1,
+                                               int32_t *out0, int32_t *out1, const int32_t *__restrict__ q,
+                                               int32_t *__restrict__ child, const int32_t *__restrict__ keep,
+                                               const int32_t *__restrict__ par_r, const int32_t *__restrict__ copy_r,
+                                               const uint32_t *__restrict__ gen_ptr, int *__restrict__ dcount,
+                                               int vblock, int vgrid)
 {
     // The mutation kernel that follows appends deferred pairs from zero.
-    if (blockIdx.x == 0 && threadIdx.x < 3) dcount[threadIdx.x] = 0;
+    if (vblock == 0 && threadIdx.x < 3) dcount[threadIdx.x] = 0;
     extern __shared__ int smem[];
     const int W = gp.W, np = gp.np, E = gp.es;
     const int nq = W >> 2;
@@ -205,8 +205,8 @@ crossover_kernel(GenParams gp, const int32_t *buf0, const int32_t *buf1, int32_t
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     int *row = s_rows + wib * 2 * W;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int warp = (vblock * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (vgrid * blockDim.x) >> 5;
     const bool active = lane < nq;
 
     // Software pipeline: the next node's rows are requested before the
@@ -325,6 +325,46 @@ crossover_kernel(GenParams gp, const int32_t *buf0, const int32_t *buf1, int32_t
         }
         __syncwarp();
     }
+}
+
+template <int EMAX>
+__global__ void __launch_bounds__(kBlock)
+crossover_kernel(GenParams gp, const int32_t *buf0, const int32_t *buf1, int32_t *out0, int32_t *out1,
+                 const int32_t *__restrict__ q, int32_t *__restrict__ child,
+                 const int32_t *__restrict__ keep, const int32_t *__restrict__ par_r,
+                 const int32_t *__restrict__ copy_r, const uint32_t *__restrict__ gen_ptr,
+                 int *__restrict__ dcount)
+{
+    crossover_body<EMAX>(gp, buf0, buf1, out0, out1, q, child, keep, par_r, copy_r, gen_ptr, dcount, blockIdx.x,
+                         gridDim.x);
+}
+
+// The member of a multi-member launch that block blockIdx.x belongs to:
+// members own consecutive block ranges, starts[k] .. starts[k + 1] - 1
+// (empty for a member with nothing to do).
+__device__ __forceinline__ int member_of_block(const int *__restrict__ starts, int count)
+{
+    const int b = (int)blockIdx.x;
+    int lo = 0, hi = count;  // starts[lo] <= b < starts[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(starts + mid) <= b) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Crossover of every member of a batch in one launch.
+template <int EMAX>
+__global__ void __launch_bounds__(kBlock)
+crossover_multi_kernel(const BatchMember *__restrict__ members, const int *__restrict__ starts, int count)
+{
+    const int k = member_of_block(starts, count);
+    const BatchMember &mb = members[k];
+    const PopState &ps = mb.ps;
+    const int b0 = __ldg(starts + k);
+    crossover_body<EMAX>(mb.gp, ps.buf[0], ps.buf[1], ps.buf[0], ps.buf[1], ps.q, ps.c, ps.keep, ps.par_r,
+                         ps.copy_r, ps.gen, ps.dcount, (int)blockIdx.x - b0, __ldg(starts + k + 1) - b0);
 }
 
 // ---------------------------------------------------------------------------
@@ -1100,18 +1140,19 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
 // best count c has (K + 1) c > deg (K the counters of the node's Misra-Gries
 // pass: 1 for degree <= 64, else 3), counts the pair in v's hint.
 template <int N>
-__global__ void __launch_bounds__(kMutBlock)
-mutation_vote_kernel(GenParams gp, int cls, const int32_t *__restrict__ row_ptr,
-                     const int32_t *__restrict__ col_idx, const int32_t *__restrict__ child,
-                     int32_t *__restrict__ q, const uint32_t *__restrict__ gen_ptr, uint32_t *__restrict__ hist,
-                     uint32_t *__restrict__ hint, const int2 *__restrict__ dlist, const int *__restrict__ dcount)
+__device__ __forceinline__ void mutation_vote_body(const GenParams &gp, int cls, const int32_t *__restrict__ row_ptr,
+                                                   const int32_t *__restrict__ col_idx,
+                                                   const int32_t *__restrict__ child, int32_t *__restrict__ q,
+                                                   const uint32_t *__restrict__ gen_ptr, uint32_t *__restrict__ hist,
+                                                   uint32_t *__restrict__ hint, const int2 *__restrict__ dlist,
+                                                   const int *__restrict__ dcount, int vblock, int vgrid)
 {
     constexpr int NW = (N + 63) / 64;
     const uint32_t g = *gen_ptr;
     const int W = gp.W;
     const int total = min(dcount[cls], defer_capacity(gp, cls));
     const int2 *list = dlist + defer_offset(gp, cls);
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    for (int t = vblock * blockDim.x + threadIdx.x; t < total; t += vgrid * blockDim.x) {
         const int2 e = list[t];
         const int v = e.x, i = e.y;
         if (!MOCD_CHECK(v >= 0 && v < gp.n && i >= 0 && i < gp.np, kCheckNode, t)) continue;
@@ -1194,6 +1235,33 @@ mutation_vote_kernel(GenParams gp, int cls, const int32_t *__restrict__ row_ptr,
         if (MOCD_CHECK(res >= 0 && res < gp.n, kCheckLabel, v)) atomicAdd(hist + (size_t)res * W + i, (unsigned)deg);
         if ((N <= 2 * kTileRows ? 2 : 4) * best > deg) atomicAdd(hint + v, 1u);
     }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kMutBlock)
+mutation_vote_kernel(GenParams gp, int cls, const int32_t *__restrict__ row_ptr,
+                     const int32_t *__restrict__ col_idx, const int32_t *__restrict__ child,
+                     int32_t *__restrict__ q, const uint32_t *__restrict__ gen_ptr, uint32_t *__restrict__ hist,
+                     uint32_t *__restrict__ hint, const int2 *__restrict__ dlist, const int *__restrict__ dcount)
+{
+    mutation_vote_body<N>(gp, cls, row_ptr, col_idx, child, q, gen_ptr, hist, hint, dlist, dcount, blockIdx.x,
+                          gridDim.x);
+}
+
+// The deferred votes of one degree class of every member of a batch.
+// (Register cap: the single-member kernel's occupancy, 5 blocks of 128
+// threads for 64 entries; 2 for 128, whose registers do not fit 3 here.)
+template <int N>
+__global__ void __launch_bounds__(kMutBlock, N <= 64 ? 5 : 2)
+mutation_vote_multi_kernel(const BatchMember *__restrict__ members, const int *__restrict__ starts, int count,
+                           int cls)
+{
+    const int k = member_of_block(starts, count);
+    const BatchMember &mb = members[k];
+    const PopState &ps = mb.ps;
+    const int b0 = __ldg(starts + k);
+    mutation_vote_body<N>(mb.gp, cls, mb.row_ptr, mb.col_idx, ps.c, ps.q, ps.gen, ps.hist, ps.hint, ps.dlist,
+                          ps.dcount, (int)blockIdx.x - b0, __ldg(starts + k + 1) - b0);
 }
 
 // The listed votes of hubs above kSharedTableMax: a warp per pair, its count
@@ -1283,6 +1351,30 @@ cudaError_t launch_crossover(const GenParams &gp, const PopState &ps, int grid, 
     return cudaGetLastError();
 }
 
+cudaError_t launch_crossover_multi(const BatchMember *members, const int *starts, int count, int blocks, int es_max,
+                                   cudaStream_t s)
+{
+    if (blocks <= 0) return cudaSuccess;
+    if (es_max <= 4)
+        crossover_multi_kernel<4><<<blocks, kBlock, crossover_smem<4>(), s>>>(members, starts, count);
+    else if (es_max <= 8)
+        crossover_multi_kernel<8><<<blocks, kBlock, crossover_smem<8>(), s>>>(members, starts, count);
+    else
+        crossover_multi_kernel<16><<<blocks, kBlock, crossover_smem<16>(), s>>>(members, starts, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vote_multi(const BatchMember *members, const int *starts, int count, int blocks, int cls,
+                              cudaStream_t s)
+{
+    if (blocks <= 0) return cudaSuccess;
+    if (cls == 0)
+        mutation_vote_multi_kernel<2 * kTileRows><<<blocks, kMutBlock, 0, s>>>(members, starts, count, 0);
+    else
+        mutation_vote_multi_kernel<kDeferMax><<<blocks, kMutBlock, 0, s>>>(members, starts, count, 1);
+    return cudaGetLastError();
+}
+
 int mutation_smem(int hash_size)
 {
     return (kMutBlock / 32) * (2 * kMaxPop + kTileRows * kTileStride + 2 * hash_size) * (int)sizeof(int);
@@ -1316,21 +1408,21 @@ void grid_for_votes(int sms, int *grid64, int *grid128)
 
 cudaError_t launch_mutation(const GenParams &gp, const PopState &ps, const int32_t *row_ptr,
                             const int32_t *col_idx, const int32_t *order, int grid, int grid64, int grid128,
-                            cudaStream_t s)
+                            cudaStream_t s, bool with_votes)
 {
     mutation_kernel<<<grid, kMutBlock, mutation_smem(gp.hash_size), s>>>(gp, row_ptr, col_idx, order, ps.c, ps.q,
                                                                        ps.gen, ps.hist, ps.acc, ps.hint, ps.dlist,
                                                                        ps.dcount);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (gp.defer_cap[0] > 0) {
+    if (with_votes && gp.defer_cap[0] > 0) {
         mutation_vote_kernel<2 * kTileRows><<<grid64, kMutBlock, 0, s>>>(gp, 0, row_ptr, col_idx, ps.c, ps.q,
                                                                            ps.gen, ps.hist, ps.hint, ps.dlist,
                                                                            ps.dcount);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    if (gp.defer_cap[1] > 0) {
+    if (with_votes && gp.defer_cap[1] > 0) {
         mutation_vote_kernel<kDeferMax><<<grid128, kMutBlock, 0, s>>>(gp, 1, row_ptr, col_idx, ps.c, ps.q, ps.gen,
                                                                         ps.hist, ps.hint, ps.dlist, ps.dcount);
         e = cudaGetLastError();

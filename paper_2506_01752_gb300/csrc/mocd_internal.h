@@ -91,6 +91,16 @@ struct GenParams {
     unsigned long long thr_m; // mutate iff u < thr_m
 };
 
+// One member of a multi-member launch (a batch of contexts): its parameters,
+// state and graph.
+struct BatchMember {
+    GenParams gp;
+    PopState ps;
+    const int32_t *row_ptr;
+    const int32_t *col_idx;
+    const int32_t *order;
+};
+
 // Launch wrappers (stream-ordered, return cudaGetLastError()).
 // init_mode 0: labels uniform in [0, n); 1: singletons then one full-rate
 // neighbour-majority step (needs the sorted, repeat-free adjacency).
@@ -99,9 +109,20 @@ cudaError_t launch_init_population(const GenParams &gp, int init_mode, const int
 cudaError_t launch_crossover(const GenParams &gp, const PopState &ps, int grid, cudaStream_t s);
 // order: the nodes in the sequence the grid-stride loop visits them
 // (degree descending), or NULL for 0..n-1 (evaluation only).
+// with_votes false: the per-pair votes of the deferred classes are left to
+// launch_vote_multi (a batch launches them for all members at once).
 cudaError_t launch_mutation(const GenParams &gp, const PopState &ps, const int32_t *row_ptr,
                             const int32_t *col_idx, const int32_t *order, int grid, int grid64, int grid128,
-                            cudaStream_t s);
+                            cudaStream_t s, bool with_votes = true);
+// Multi-member launches of a batch: member k owns blocks starts[k] ..
+// starts[k + 1] - 1 of the launch's `blocks` (each member's own grid for
+// the stage; zero for a member with nothing to do).
+cudaError_t launch_crossover_multi(const BatchMember *members, const int *starts, int count, int blocks, int es_max,
+                                   cudaStream_t s);
+cudaError_t launch_vote_multi(const BatchMember *members, const int *starts, int count, int blocks, int cls,
+                              cudaStream_t s);
+cudaError_t launch_evaluate_multi(const BatchMember *members, const int *starts, int count, int blocks,
+                                  cudaStream_t s);
 // Resident-block grids of the two per-pair vote kernels (degree classes
 // 33..64 and 65..128).
 void grid_for_votes(int sms, int *grid64, int *grid128);

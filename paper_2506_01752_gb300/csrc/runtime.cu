@@ -1226,11 +1226,18 @@ struct mocd_batch {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    // Selection of every member in one multi-population launch after the
-    // members' kernel chains, instead of one selection at the end of each.
-    bool merged_select = false;
+    // Form 0: each member's kernel chain, selection included, on its own
+    // graph branch. Form 1: the selections of all members in one
+    // multi-population launch after the chains. Form 2: also crossover, the
+    // deferred mutation votes and the evaluation of all members in one
+    // multi-member launch each; only the mutation kernels stay per member.
+    int form = 0;
     GenParams *d_gp = nullptr;  // [count], for the merged selection
     PopState *d_ps = nullptr;
+    BatchMember *d_members = nullptr;  // [count], for the multi-member launches
+    int *d_starts = nullptr;           // [4][count + 1] block ranges: crossover, votes 33..64, 65..128, evaluation
+    int blocks[4] = {0, 0, 0, 0};      // blocks of each multi-member launch
+    int es_max = 0;
     std::vector<mocd_ctx *> ctx;
     std::vector<int32_t> version;
     std::vector<cudaStream_t> branch;
@@ -1246,29 +1253,66 @@ static int batch_build(mocd_batch *b)
     if (b->graph) cudaGraphDestroy(b->graph);
     b->exec = nullptr;
     b->graph = nullptr;
-    if (b->merged_select) {
-        // The members' current parameters and states, for the merged selection.
+    const int count = (int)b->ctx.size();
+    if (b->form >= 1) {
+        // The members' current parameters and states, for the merged launches.
         std::vector<GenParams> gps;
         std::vector<PopState> pss;
-        for (mocd_ctx *c : b->ctx) {
+        std::vector<BatchMember> mbs;
+        std::vector<int> starts(4 * (size_t)(count + 1), 0);
+        b->es_max = 0;
+        for (int i = 0; i < count; ++i) {
+            mocd_ctx *c = b->ctx[(size_t)i];
             gps.push_back(c->gp);
             pss.push_back(c->ps);
+            mbs.push_back(BatchMember{c->gp, c->ps, c->d_row_ptr, c->d_col_idx, c->d_order});
+            b->es_max = std::max(b->es_max, c->gp.es);
+            // Per member and stage: its own grid (a deferred class's votes get
+            // about one thread per four listed pairs at full capacity, at most
+            // its single-member grid).
+            const int g[4] = {
+                c->grid_cross,
+                c->gp.defer_cap[0] > 0 ? std::min(c->grid_vote64, (c->gp.defer_cap[0] + 4 * 128 - 1) / (4 * 128)) : 0,
+                c->gp.defer_cap[1] > 0 ? std::min(c->grid_vote128, (c->gp.defer_cap[1] + 4 * 128 - 1) / (4 * 128)) : 0,
+                c->grid_eval_intra};
+            for (int st = 0; st < 4; ++st)
+                starts[(size_t)st * (count + 1) + i + 1] = starts[(size_t)st * (count + 1) + i] + g[st];
         }
+        for (int st = 0; st < 4; ++st) b->blocks[st] = starts[(size_t)st * (count + 1) + count];
         CK(cudaMemcpyAsync(b->d_gp, gps.data(), sizeof(GenParams) * gps.size(), cudaMemcpyHostToDevice, b->stream));
         CK(cudaMemcpyAsync(b->d_ps, pss.data(), sizeof(PopState) * pss.size(), cudaMemcpyHostToDevice, b->stream));
+        CK(cudaMemcpyAsync(b->d_members, mbs.data(), sizeof(BatchMember) * mbs.size(), cudaMemcpyHostToDevice,
+                           b->stream));
+        CK(cudaMemcpyAsync(b->d_starts, starts.data(), sizeof(int) * starts.size(), cudaMemcpyHostToDevice,
+                           b->stream));
         CK(cudaStreamSynchronize(b->stream));
     }
+    const int *st_cross = b->d_starts, *st_v64 = b->d_starts + (count + 1), *st_v128 = b->d_starts + 2 * (count + 1),
+              *st_eval = b->d_starts + 3 * (count + 1);
     CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     int rc = MOCD_OK;
-    cudaError_t e = cudaEventRecord(b->fork, b->stream);
-    for (size_t i = 0; i < b->ctx.size() && rc == MOCD_OK && e == cudaSuccess; ++i) {
-        e = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
-        if (e == cudaSuccess) rc = issue_generation(b->ctx[i], b->branch[i], false, !b->merged_select);
-        if (rc == MOCD_OK && e == cudaSuccess) e = cudaEventRecord(b->join[i], b->branch[i]);
-        if (rc == MOCD_OK && e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join[i], 0);
+    cudaError_t e = cudaSuccess;
+    if (b->form == 2) e = launch_crossover_multi(b->d_members, st_cross, count, b->blocks[0], b->es_max, b->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->stream);
+    for (int i = 0; i < count && rc == MOCD_OK && e == cudaSuccess; ++i) {
+        mocd_ctx *c = b->ctx[(size_t)i];
+        e = cudaStreamWaitEvent(b->branch[(size_t)i], b->fork, 0);
+        if (e != cudaSuccess) break;
+        if (b->form == 2)
+            e = launch_mutation(c->gp, c->ps, c->d_row_ptr, c->d_col_idx, c->d_order, c->grid_mut, c->grid_vote64,
+                                c->grid_vote128, b->branch[(size_t)i], false);
+        else
+            rc = issue_generation(c, b->branch[(size_t)i], false, b->form == 0);
+        if (rc == MOCD_OK && e == cudaSuccess) e = cudaEventRecord(b->join[(size_t)i], b->branch[(size_t)i]);
+        if (rc == MOCD_OK && e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join[(size_t)i], 0);
     }
-    if (rc == MOCD_OK && e == cudaSuccess && b->merged_select)
-        e = launch_select_multi(b->d_gp, b->d_ps, (int)b->ctx.size(), 1, b->stream);
+    if (rc == MOCD_OK && e == cudaSuccess && b->form == 2) {
+        e = launch_vote_multi(b->d_members, st_v64, count, b->blocks[1], 0, b->stream);
+        if (e == cudaSuccess) e = launch_vote_multi(b->d_members, st_v128, count, b->blocks[2], 1, b->stream);
+        if (e == cudaSuccess) e = launch_evaluate_multi(b->d_members, st_eval, count, b->blocks[3], b->stream);
+    }
+    if (rc == MOCD_OK && e == cudaSuccess && b->form >= 1)
+        e = launch_select_multi(b->d_gp, b->d_ps, count, 1, b->stream);
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (rc || e != cudaSuccess || e2 != cudaSuccess) {
@@ -1314,6 +1358,12 @@ int mocd_batch_create(mocd_batch **out, int32_t count, mocd_ctx *const *ctxs, vo
         b->d_gp = static_cast<GenParams *>(p);
         if (dev_alloc(&p, sizeof(PopState) * (size_t)count, b->stream) != cudaSuccess) return fail(MOCD_ERR_OUT_OF_MEMORY);
         b->d_ps = static_cast<PopState *>(p);
+        if (dev_alloc(&p, sizeof(BatchMember) * (size_t)count, b->stream) != cudaSuccess)
+            return fail(MOCD_ERR_OUT_OF_MEMORY);
+        b->d_members = static_cast<BatchMember *>(p);
+        if (dev_alloc(&p, sizeof(int) * 4 * (size_t)(count + 1), b->stream) != cudaSuccess)
+            return fail(MOCD_ERR_OUT_OF_MEMORY);
+        b->d_starts = static_cast<int *>(p);
     }
     for (int32_t i = 0; i < count; ++i) {
         // Work already issued on a member's own stream finishes first.
@@ -1357,7 +1407,7 @@ int mocd_batch_autotune(mocd_batch *b, int32_t generations_per_trial, int32_t *n
 {
     if (!b || generations_per_trial < 1) return MOCD_ERR_INVALID_ARG;
     static const int kShapes[] = {1, 2, 4, 8, 16};
-    b->merged_select = false;  // the shapes are compared in the per-member form
+    b->form = 0;  // the shapes are compared in the per-member form
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     CK(cudaEventCreate(&t0));
     CK(cudaEventCreate(&t1));
@@ -1384,38 +1434,44 @@ int mocd_batch_autotune(mocd_batch *b, int32_t generations_per_trial, int32_t *n
             best = shape;
         }
     }
-    // Then the selection form at that shape: per member, or merged.
-    bool best_merged = false;
+    // Then the form at that shape: per member, merged selection, or
+    // multi-member launches for every stage but the mutation kernel.
+    int best_form = 0;
     if (rc == MOCD_OK) {
         for (mocd_ctx *c : b->ctx) {
             c->nodes_per_warp = best;
             size_grids(c);
         }
-        b->merged_select = true;
-        float ms = 0.0f;
-        if ((rc = batch_build(b)) == MOCD_OK && (rc = mocd_batch_generation(b, 1)) == MOCD_OK) {
+        for (int form = 1; form <= 2 && rc == MOCD_OK; ++form) {
+            b->form = form;
+            float ms = 0.0f;
+            if ((rc = batch_build(b)) != MOCD_OK || (rc = mocd_batch_generation(b, 1)) != MOCD_OK) break;
             if (cudaEventRecord(t0, b->stream) != cudaSuccess) rc = MOCD_ERR_CUDA;
             if (rc == MOCD_OK) rc = mocd_batch_generation(b, generations_per_trial);
             if (rc == MOCD_OK &&
                 (cudaEventRecord(t1, b->stream) != cudaSuccess || cudaEventSynchronize(t1) != cudaSuccess))
                 rc = MOCD_ERR_CUDA;
             if (rc == MOCD_OK) cudaEventElapsedTime(&ms, t0, t1);
-            best_merged = rc == MOCD_OK && ms < best_ms;
+            if (rc == MOCD_OK && ms < best_ms) {
+                best_ms = ms;
+                best_form = form;
+            }
         }
-        b->merged_select = best_merged;
+        b->form = best_form;
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
     if (rc) return rc;
-    if ((rc = mocd_batch_configure(b, best, best_merged ? 1 : 0))) return rc;
+    if ((rc = mocd_batch_configure(b, best, best_form))) return rc;
     if (nodes_per_warp) *nodes_per_warp = best;
     return MOCD_OK;
 }
 
-int mocd_batch_configure(mocd_batch *b, int32_t nodes_per_warp, int32_t merged_select)
+int mocd_batch_configure(mocd_batch *b, int32_t nodes_per_warp, int32_t form)
 {
     if (!b || (nodes_per_warp != 1 && nodes_per_warp != 2 && nodes_per_warp != 4 && nodes_per_warp != 8 &&
-               nodes_per_warp != 16))
+               nodes_per_warp != 16) ||
+        form < 0 || form > 2)
         return MOCD_ERR_INVALID_ARG;
     for (size_t i = 0; i < b->ctx.size(); ++i)
         if (!b->ctx[i]->ready || b->ctx[i]->version != b->version[i]) return MOCD_ERR_NOT_READY;
@@ -1427,15 +1483,15 @@ int mocd_batch_configure(mocd_batch *b, int32_t nodes_per_warp, int32_t merged_s
         drop_graphs(c);
         if ((rc = build_graph(c))) return rc;
     }
-    b->merged_select = merged_select != 0;
+    b->form = form;
     return batch_build(b);
 }
 
-int mocd_batch_form(mocd_batch *b, int32_t *nodes_per_warp, int32_t *merged_select)
+int mocd_batch_form(mocd_batch *b, int32_t *nodes_per_warp, int32_t *form)
 {
     if (!b || b->ctx.empty()) return MOCD_ERR_INVALID_ARG;
     if (nodes_per_warp) *nodes_per_warp = b->ctx[0]->nodes_per_warp;
-    if (merged_select) *merged_select = b->merged_select ? 1 : 0;
+    if (form) *form = b->form;
     return MOCD_OK;
 }
 
@@ -1448,6 +1504,8 @@ void mocd_batch_destroy(mocd_batch *b)
     if (b->graph) cudaGraphDestroy(b->graph);
     dev_free(b->d_gp, b->stream);
     dev_free(b->d_ps, b->stream);
+    dev_free(b->d_members, b->stream);
+    dev_free(b->d_starts, b->stream);
     if (b->stream) cudaStreamSynchronize(b->stream);
     for (cudaStream_t st : b->branch) cudaStreamDestroy(st);
     for (cudaEvent_t ev : b->join) cudaEventDestroy(ev);

@@ -45,6 +45,8 @@ def _run(autotune, merged=None):
             if merged is not None:
                 mocd.batch_configure(b, 2, merged)
                 assert mocd.batch_form(b) == (2, merged)
+                with pytest.raises(mocd.MocdError):
+                    mocd.batch_configure(b, 2, 3)
             mocd.batch_generation(b, 4)
             mocd.batch_synchronize(b)
             for c, ((rp, ci), kw) in zip(ctxs, inst):
@@ -75,11 +77,13 @@ def test_batch_after_autotune_matches_oracle():
     _run(autotune=True)
 
 
-@pytest.mark.parametrize("merged", [False, True])
-def test_batch_selection_forms_match_oracle(merged):
-    """The per-member selections and the one merged multi-population
-    selection launch give the same generations (the oracle's)."""
-    _run(autotune=False, merged=merged)
+@pytest.mark.parametrize("form", [0, 1, 2])
+def test_batch_forms_match_oracle(form):
+    """Per-member chains, the merged multi-population selection and the
+    multi-member crossover, vote, evaluation and selection launches give the
+    same generations (the oracle's); the members differ in size, N_p and E_S
+    (3, 4 and 5: the multi-member crossover takes the general E_S form)."""
+    _run(autotune=False, merged=form)
 
 
 def test_batch_rejects_bad_members():
@@ -110,11 +114,13 @@ def test_full_batch_of_64_sampled_against_oracle():
             mocd.population_init(c, mocd.Params(seed=k))
         b = mocd.batch_create(ctxs)
         mocd.batch_autotune(b, 1)
+        shape, form = mocd.batch_form(b)
         mocd.batch_destroy(b)
         for k, c in enumerate(ctxs):
             mocd.population_init(c, mocd.Params(seed=k))
         b = mocd.batch_create(ctxs)
         try:
+            mocd.batch_configure(b, shape, form)
             mocd.batch_generation(b, 2)
             mocd.batch_synchronize(b)
         finally:

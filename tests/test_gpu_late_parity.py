@@ -126,8 +126,9 @@ def test_lfr_1m_generation_100():
 
 def test_batch64_every_job_generation_20():
     """The batched-jobs workload (64 uneven jobs, n 1e3-5e4, N_p = 100 each)
-    in the autotuned launch shape: every one of the 64 jobs at generation 20
-    of a batched run, offspring, population and front bit for bit."""
+    in the autotuned launch shape with the multi-member launches (form 2):
+    every one of the 64 jobs at generation 20 of a batched run, offspring,
+    population and front bit for bit."""
     G = 20
     insts = synth.batch_instances(64, seed=0)
     ctxs = [mocd.graph_upload(rp, ci) for rp, ci, _, _ in insts]
@@ -136,11 +137,13 @@ def test_batch64_every_job_generation_20():
             mocd.population_init(c, mocd.Params(seed=k))
         b = mocd.batch_create(ctxs)
         mocd.batch_autotune(b, 1)
+        shape, _ = mocd.batch_form(b)
         mocd.batch_destroy(b)
         for k, c in enumerate(ctxs):
             mocd.population_init(c, mocd.Params(seed=k))
         b = mocd.batch_create(ctxs)
         try:
+            mocd.batch_configure(b, shape, 2)
             mocd.batch_generation(b, G - 1)
             mocd.batch_synchronize(b)
             states = []
