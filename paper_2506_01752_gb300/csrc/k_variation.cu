@@ -157,7 +157,7 @@ __device__ __forceinline__ int kth_tied(const int (&x)[EMAX], int E, int best, i
 }
 
 template <int EMAX>
-__device__ __forceinline__ void crossover_body(const GenParams &gp, const int32_t *buf0, const int32_t *buf1,
+__device__ __forceinline__ void crossover_body(const GenParams gp, const int32_t *buf0, const int32_t *buf1,
                                                int32_t *out0, int32_t *out1, const int32_t *__restrict__ q,
                                                int32_t *__restrict__ child, const int32_t *__restrict__ keep,
                                                const int32_t *__restrict__ par_r, const int32_t *__restrict__ copy_r,
@@ -1140,7 +1140,7 @@ mutation_kernel(GenParams gp, const int32_t *__restrict__ row_ptr, const int32_t
 // best count c has (K + 1) c > deg (K the counters of the node's Misra-Gries
 // pass: 1 for degree <= 64, else 3), counts the pair in v's hint.
 template <int N>
-__device__ __forceinline__ void mutation_vote_body(const GenParams &gp, int cls, const int32_t *__restrict__ row_ptr,
+__device__ __forceinline__ void mutation_vote_body(const GenParams gp, int cls, const int32_t *__restrict__ row_ptr,
                                                    const int32_t *__restrict__ col_idx,
                                                    const int32_t *__restrict__ child, int32_t *__restrict__ q,
                                                    const uint32_t *__restrict__ gen_ptr, uint32_t *__restrict__ hist,
