@@ -47,7 +47,7 @@ struct SelShared {
     int order[kMaxPoints];       // (rank, crowding desc, index) order
     // scratch by sorted position
     unsigned long long sa[kMaxPoints], sb[kMaxPoints];
-    int ia[kMaxPoints], ib[kMaxPoints];
+    int ib[kMaxPoints];
     unsigned long long wscan[kSelWarps];
     int wscan2[kSelWarps];
     int fsize[kMaxPoints + 1];

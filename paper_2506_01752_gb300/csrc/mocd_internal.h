@@ -69,7 +69,8 @@ struct PopState {
     int32_t *front;           // [2 + kMaxPop]: count, best, members (P positions)
     int64_t *fint;            // [2][kMaxPop]: intra, S of each front member
     double *fval;             // [2][kMaxPop]: f1, f2 of each front member
-    uint32_t *hint;           // [n]: (mutating pairs << 16) | pairs with a label above deg / 4, last generation
+    uint32_t *hint;           // [n]: (mutating pairs << 16) | pairs the Misra-Gries pass settles (a label above
+                              // deg / (K + 1), K its counters), last generation; nodes of degree > 32
     int2 *dlist;              // deferred mutation votes (node, child): class 0 then class 1
     int *dcount;              // [3]: deferred votes appended this generation: degree 33..64, 65..128, hubs
     int *hub_table;           // hub_warps x 2 hub_hs: per-warp count tables of the hub votes
