@@ -378,17 +378,18 @@ crossover_multi_kernel(const BatchMember *__restrict__ members, const int *__res
 // selected, each lane sorts its own pair's labels in registers with a
 // merge-exchange network of 8, 12, .., 28 or 32 entries (the smallest that
 // holds the degree) and reads the tied labels off the runs, all pairs at
-// once; when few are, the whole warp votes on two
-// pairs at a time (one neighbour per lane grouped by __match_any_sync, the
-// pick(u, t)-th tied label by removing minima or, for deep ranks, by sorting
-// the tied labels across the warp). Degree > 32: when the node's history says
-// it pays, a Misra-Gries summary with K counters (K = 1 up to degree 64, 3
-// above) and an exact recount of its survivors settle every pair whose best
-// count c has (K + 1) c > deg (every label reaching c is then a candidate);
-// the other pairs of degree 33..kDeferMax
-// are listed for mutation_vote_kernel (one pair per thread, labels sorted in
-// registers), and those of higher degree take a count table in shared
-// memory, one pair at a time.
+// once; when few are, the whole warp votes on two pairs at a time (one
+// neighbour per lane grouped by __match_any_sync, the pick(u, t)-th tied
+// label by removing minima or, for deep ranks, by sorting the tied labels
+// across the warp). Degree > 32: when the node's history says it pays, a
+// Misra-Gries summary with K counters (K = 1 up to degree 64, 3 above) and an
+// exact recount of its survivors settle every pair whose best count c has
+// (K + 1) c > deg (every label reaching c is then a candidate); the other
+// pairs of degree 33..kDeferMax are listed for mutation_vote_kernel (one pair
+// per thread, labels sorted in registers), those of degree kDeferMax + 1 ..
+// kSharedTableMax take a count table in shared memory, one pair at a time,
+// and those above are listed for mutation_hub_kernel (a warp per pair, its
+// count table in global scratch).
 // ---------------------------------------------------------------------------
 
 // The ka-th and kb-th smallest of the distinct labels held by the lanes of
