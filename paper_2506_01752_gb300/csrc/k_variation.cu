@@ -1398,10 +1398,16 @@ int grid_for_mutation(int sms, int hash_size, int *smem_bytes)
     return sms * per_sm;
 }
 
-void grid_for_votes(int sms, int *grid64, int *grid128)
+void grid_for_votes(int sms, int vote_n0, int *grid64, int *grid128)
 {
     int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, mutation_vote_kernel<2 * kTileRows>, kMutBlock, 0);
+    switch (vote_n0) {
+    case 40: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, mutation_vote_kernel<40>, kMutBlock, 0); break;
+    case 48: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, mutation_vote_kernel<48>, kMutBlock, 0); break;
+    case 56: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, mutation_vote_kernel<56>, kMutBlock, 0); break;
+    default:
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, mutation_vote_kernel<2 * kTileRows>, kMutBlock, 0);
+    }
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, mutation_vote_kernel<kDeferMax>, kMutBlock, 0);
     *grid64 = sms * (a < 1 ? 1 : a);
     *grid128 = sms * (b < 1 ? 1 : b);
@@ -1417,9 +1423,25 @@ cudaError_t launch_mutation(const GenParams &gp, const PopState &ps, const int32
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (with_votes && gp.defer_cap[0] > 0) {
-        mutation_vote_kernel<2 * kTileRows><<<grid64, kMutBlock, 0, s>>>(gp, 0, row_ptr, col_idx, ps.c, ps.q,
-                                                                           ps.gen, ps.hist, ps.hint, ps.dlist,
-                                                                           ps.dcount);
+        // The class's network holds the graph's largest degree in it.
+        switch (gp.vote_n0) {
+        case 40:
+            mutation_vote_kernel<40><<<grid64, kMutBlock, 0, s>>>(gp, 0, row_ptr, col_idx, ps.c, ps.q, ps.gen,
+                                                                  ps.hist, ps.hint, ps.dlist, ps.dcount);
+            break;
+        case 48:
+            mutation_vote_kernel<48><<<grid64, kMutBlock, 0, s>>>(gp, 0, row_ptr, col_idx, ps.c, ps.q, ps.gen,
+                                                                  ps.hist, ps.hint, ps.dlist, ps.dcount);
+            break;
+        case 56:
+            mutation_vote_kernel<56><<<grid64, kMutBlock, 0, s>>>(gp, 0, row_ptr, col_idx, ps.c, ps.q, ps.gen,
+                                                                  ps.hist, ps.hint, ps.dlist, ps.dcount);
+            break;
+        default:
+            mutation_vote_kernel<2 * kTileRows><<<grid64, kMutBlock, 0, s>>>(gp, 0, row_ptr, col_idx, ps.c, ps.q,
+                                                                               ps.gen, ps.hist, ps.hint, ps.dlist,
+                                                                               ps.dcount);
+        }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

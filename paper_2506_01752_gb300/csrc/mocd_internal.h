@@ -86,6 +86,8 @@ struct GenParams {
     int defer_cap[3];         // deferred-vote capacity per class: N_p x nodes of the class
     int hub_hs;               // slots of a hub count table (power of two >= 2 dmax; 0: no hubs)
     int hub_warps;            // warps of mutation_hub_kernel (one table slice each)
+    int vote_n0;              // entries of the degree 33..64 vote's sorting network: the smallest multiple
+                              // of 8 that holds the graph's largest degree in that class (40, 48, 56 or 64)
     int64_t m;                // edges
     uint32_t key0, key1;      // Philox key (seed)
     unsigned long long thr_c; // crossover iff u <= thr_c
@@ -126,7 +128,7 @@ cudaError_t launch_evaluate_multi(const BatchMember *members, const int *starts,
                                   cudaStream_t s);
 // Resident-block grids of the two per-pair vote kernels (degree classes
 // 33..64 and 65..128).
-void grid_for_votes(int sms, int *grid64, int *grid128);
+void grid_for_votes(int sms, int vote_n0, int *grid64, int *grid128);
 // hist: label-major [n][W] (label_major) or individual-major [count][n],
 // zeroed by the caller.
 cudaError_t launch_evaluate(int n, int W, int count, const int32_t *row_ptr, const int32_t *col_idx,

@@ -341,6 +341,10 @@ int prepare_population(mocd_ctx *c, const mocd_params *p)
     gp.defer_cap[2] = (int)((int64_t)p->pop_size * c->n_defer[2]);
     gp.hub_hs = hub_hs;
     gp.hub_warps = hub_warps;
+    {
+        const int d0 = (int)std::min<int64_t>(std::max<int64_t>(c->dmax, 2 * 16 + 1), 2 * 32);  // degree class 33..64
+        gp.vote_n0 = (d0 + 7) / 8 * 8;
+    }
     gp.m = c->m;
     gp.key0 = (uint32_t)p->seed;
     gp.key1 = (uint32_t)(p->seed >> 32);
@@ -348,7 +352,7 @@ int prepare_population(mocd_ctx *c, const mocd_params *p)
     gp.thr_m = (unsigned long long)floor(p->p_mutation * 4294967296.0);
     c->occ_eval = grid_for_eval(c->sms);
     c->occ_eval_intra = grid_for_eval_intra(c->sms);
-    grid_for_votes(c->sms, &c->grid_vote64, &c->grid_vote128);
+    grid_for_votes(c->sms, gp.vote_n0, &c->grid_vote64, &c->grid_vote128);
     c->occ_cross = grid_for_crossover(c->sms, gp.es);
     int smem = 0;
     c->occ_mut = grid_for_mutation(c->sms, gp.hash_size, &smem);

@@ -212,6 +212,14 @@ def test_generations_match_oracle(gname, G, kw):
     ("ladder", 3, dict(pop_size=40, p_mutation=1.0)),      # network-size boundaries, two rounds of pairs
     ("ladder", 4, dict(pop_size=100, seed=9)),
     ("lfr-3k", 2, dict(pop_size=50, seed=0xDEADBEEF12345678)),  # both key words non-zero
+    # the degree 33..64 vote sorts as many entries as the graph's largest
+    # degree needs (40, 48, 56 or 64): each size at both ends of its range
+    ("ladder40", 3, dict(pop_size=40, p_mutation=1.0)),
+    ("ladder48", 3, dict(pop_size=40, p_mutation=1.0)),
+    ("ladder56", 3, dict(pop_size=40, p_mutation=1.0)),
+    ("ladder64", 3, dict(pop_size=40, p_mutation=1.0)),
+    ("k49", 3, dict(pop_size=30, p_mutation=0.5)),
+    ("k57", 3, dict(pop_size=30, p_mutation=0.5)),
 ])
 def test_extreme_graphs_match_oracle(gname, G, kw):
     rp, ci = {
@@ -219,7 +227,13 @@ def test_extreme_graphs_match_oracle(gname, G, kw):
         "one-edge": lambda: synth.csr_from_edges(3000, [17], [2950]),
         "k40": lambda: complete_graph(40),
         "k33": lambda: complete_graph(33),
+        "k49": lambda: complete_graph(49),
+        "k57": lambda: complete_graph(57),
         "ladder": degree_ladder,
+        "ladder40": lambda: degree_ladder((5, 33, 40)),
+        "ladder48": lambda: degree_ladder((33, 41, 48)),
+        "ladder56": lambda: degree_ladder((33, 49, 56)),
+        "ladder64": lambda: degree_ladder((33, 57, 64)),
         "lfr-3k": GRAPHS["lfr-3k"],
     }[gname]()
     gp, op = _params(**kw)
