@@ -132,19 +132,20 @@ def algorithmic_bytes(n: int, m: int, np_: int, p_mut: float, es: int = 4) -> di
 def access_bytes(n: int, m: int, np_: int, p_mut: float) -> dict:
     """Per-launch bytes of the node-major kernels as built (rows of W int32
     labels per node, the CSR streamed once per population, each undirected
-    edge read from its lower end), with no reuse beyond what a kernel stages
-    explicitly."""
+    edge read once by the evaluation), with no reuse beyond what a kernel
+    stages explicitly."""
     W = (np_ + 3) & ~3
     csr = 4 * (n + 1) + 4 * 2 * m
+    oriented = 4 * (n + 1) + 4 * m + 4 * n  # the evaluation's oriented CSR and the node order
     return {
         # P half + Q rows in, next P + children rows out
         "crossover": 16 * W * n,
         # own row in, Q row out, each selected pair's neighbour labels, CSR, and the degree-histogram
         # additions of every child's final label (read-modify-write of a 4-byte cell)
         "mutation": 8 * W * n + 4 * p_mut * np_ * 2 * m + csr + 8 * np_ * n,
-        # own rows, one neighbour row per undirected edge (from its lower end), CSR, and the sweep
-        # of the [n][W] degree histogram that forms sum_c D_c^2
-        "evaluate": 4 * W * n + 4 * W * m + csr + 4 * W * n,
+        # own rows, one neighbour row per undirected edge (the oriented CSR lists each edge once),
+        # that CSR, and the sweep of the [n][W] degree histogram that forms sum_c D_c^2
+        "evaluate": 4 * W * n + 4 * W * m + oriented + 4 * W * n,
         "select": 0,
     }
 

@@ -4,12 +4,18 @@
 // For each individual i the kernel accumulates
 //   intra_i = #{{v, u} in E : L_i(v) = L_i(u)}   (= sum_c |E(c)|)
 //   S_i     = sum_c D_c^2,  D_c = sum_{v : L_i(v) = c} deg v
-// Each undirected edge is counted once, from its lower endpoint: a warp reads
-// the label rows of the neighbours u > v only, half of the adjacency.
-// exactly in integers. Layout is node-major: a warp owns node v and lane q
-// holds the int4 of labels of individuals 4q..4q+3, so each neighbour u costs
-// one coalesced row read of all individuals' labels instead of N_p scattered
-// 4-byte gathers, and the CSR is streamed once per population, not once per
+// exactly in integers. Each undirected edge is counted once, from one
+// endpoint: with the full adjacency (the initial population, mocd_evaluate)
+// a warp reads the label rows of the neighbours u > v only; the offspring
+// evaluation inside a generation walks an oriented adjacency that lists
+// every edge once, at its endpoint of lower (degree, id), so the rows it
+// reads are the higher-degree endpoints' -- fewer distinct rows, each read
+// more often, which keeps more of them in L2.
+//
+// Layout is node-major: a warp owns node v and lane q holds the int4 of
+// labels of individuals 4q..4q+3, so each neighbour u costs one coalesced
+// row read of all individuals' labels instead of N_p scattered 4-byte
+// gathers, and the CSR is streamed once per population, not once per
 // individual.
 //
 // S without a sweep over the histogram: when node v adds deg(v) to D_c, the
@@ -81,8 +87,9 @@ __device__ __forceinline__ void evaluate_body(int n, int W, int count, const int
         for (int e0 = beg; e0 < end; e0 += 32) {
             const int cnt = min(32, end - e0);
             const int my_u = lane < cnt ? __ldg(col_idx + e0 + lane) : 0;
-            // Keep the neighbours u > v of this chunk, compacted.
-            const bool up = lane < cnt && my_u > v && MOCD_CHECK(my_u < n, kCheckNode, v);
+            // Keep the neighbours whose rows v reads, compacted: u > v of the
+            // full adjacency, or every entry of the oriented one.
+            const bool up = lane < cnt && (!COUNT_D || my_u > v) && MOCD_CHECK(my_u < n, kCheckNode, v);
             const unsigned upm = __ballot_sync(0xffffffffu, up);
             const int cu = __popc(upm);
             if (up) nb[__popc(upm & lt)] = my_u;
@@ -192,7 +199,7 @@ evaluate_multi_kernel(const BatchMember *__restrict__ members, const int *__rest
     }
     const BatchMember &mb = members[lo];
     const int b0 = __ldg(starts + lo);
-    evaluate_body<true, false>(mb.gp.n, mb.gp.W, mb.gp.np, mb.row_ptr, mb.col_idx, mb.ps.q, mb.ps.hist, mb.ps.acc,
+    evaluate_body<true, false>(mb.gp.n, mb.gp.W, mb.gp.np, mb.eptr, mb.eidx, mb.ps.q, mb.ps.hist, mb.ps.acc,
                                mb.order, bk - b0, __ldg(starts + lo + 1) - b0);
 }
 
@@ -237,11 +244,11 @@ cudaError_t launch_evaluate_multi(const BatchMember *members, const int *starts,
     return cudaGetLastError();
 }
 
-cudaError_t launch_evaluate_offspring(int n, int W, int count, const int32_t *row_ptr, const int32_t *col_idx,
+cudaError_t launch_evaluate_offspring(int n, int W, int count, const int32_t *eptr, const int32_t *eidx,
                                       const int32_t *labels, uint32_t *hist, unsigned long long *acc,
                                       int grid, cudaStream_t s, const int32_t *order)
 {
-    evaluate_kernel<true, false><<<grid, kBlock, 0, s>>>(n, W, count, row_ptr, col_idx, labels, hist, acc, order);
+    evaluate_kernel<true, false><<<grid, kBlock, 0, s>>>(n, W, count, eptr, eidx, labels, hist, acc, order);
     return cudaGetLastError();
 }
 

@@ -102,6 +102,8 @@ struct BatchMember {
     const int32_t *row_ptr;
     const int32_t *col_idx;
     const int32_t *order;
+    const int32_t *eptr;  // the offspring evaluation's oriented adjacency (mocd_ctx::d_eptr / d_eidx)
+    const int32_t *eidx;
 };
 
 // Launch wrappers (stream-ordered, return cudaGetLastError()).
@@ -173,8 +175,9 @@ int grid_for_eval_intra(int sms);
 // Objectives of the offspring inside a generation: the mutation kernel has
 // already added every child's degrees to the label-major histogram (and
 // cleared acc); one launch counts intra, then forms S from the histogram and
-// zeroes it.
-cudaError_t launch_evaluate_offspring(int n, int W, int count, const int32_t *row_ptr, const int32_t *col_idx,
+// zeroes it. eptr / eidx: the oriented adjacency, each undirected edge once
+// (mocd_ctx::d_eptr / d_eidx).
+cudaError_t launch_evaluate_offspring(int n, int W, int count, const int32_t *eptr, const int32_t *eidx,
                                       const int32_t *labels, uint32_t *hist, unsigned long long *acc,
                                       int grid, cudaStream_t s, const int32_t *order);
 int grid_for_crossover(int sms, int es);

@@ -45,6 +45,12 @@ struct mocd_ctx {
     int32_t *d_row_ptr = nullptr;
     int32_t *d_col_idx = nullptr;
     int32_t *d_order = nullptr;   // nodes by degree, descending
+    // The offspring evaluation's adjacency: each undirected edge once, listed
+    // at its endpoint of lower (degree, id), so that the label rows it reads
+    // are those of the higher-degree endpoints (fewer, each read more often:
+    // more of them stay in L2). eptr [n + 1], eidx [m].
+    int32_t *d_eptr = nullptr;
+    int32_t *d_eidx = nullptr;
 
     // Population.
     bool ready = false;
@@ -386,7 +392,7 @@ int issue_generation(mocd_ctx *c, cudaStream_t st, bool events, bool with_select
     CK(launch_mutation(gp, ps, c->d_row_ptr, c->d_col_idx, c->d_order, c->grid_mut, c->grid_vote64,
                        c->grid_vote128, st));
     if (events) CK(mark(c, 2, st));
-    CK(launch_evaluate_offspring(gp.n, gp.W, gp.np, c->d_row_ptr, c->d_col_idx, ps.q, ps.hist, ps.acc,
+    CK(launch_evaluate_offspring(gp.n, gp.W, gp.np, c->d_eptr, c->d_eidx, ps.q, ps.hist, ps.acc,
                                  c->grid_eval_intra, st, c->d_order));
     if (events) CK(mark(c, 3, st));
     if (!with_select) return MOCD_OK;  // a batch selects all its members in one launch
@@ -935,6 +941,42 @@ int mocd_graph_upload(mocd_ctx **out, int64_t n, const int64_t *row_ptr, const i
     if (cudaMemcpyAsync(c->d_order, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream) !=
         cudaSuccess)
         return fail(MOCD_ERR_CUDA);
+    // The offspring evaluation's oriented adjacency: v lists u when (deg u, u)
+    // > (deg v, v), a strict total order, so every undirected edge is listed
+    // at exactly one endpoint.
+    std::vector<int32_t> eptr((size_t)n + 1, 0), eidx((size_t)(nnz / 2));
+    {
+        auto above = [&](int64_t v, int64_t u) {
+            const int64_t dv = row_ptr[v + 1] - row_ptr[v], du = row_ptr[u + 1] - row_ptr[u];
+            return du > dv || (du == dv && u > v);
+        };
+        parallel_rows(row_ptr, n, [&](int64_t v0, int64_t v1) {
+            for (int64_t v = v0; v < v1; ++v) {
+                int32_t k = 0;
+                for (int64_t q = row_ptr[v]; q < row_ptr[v + 1]; ++q) k += above(v, src[q]) ? 1 : 0;
+                eptr[(size_t)v + 1] = k;
+            }
+        });
+        for (int64_t v = 0; v < n; ++v) eptr[(size_t)v + 1] += eptr[(size_t)v];
+        parallel_rows(row_ptr, n, [&](int64_t v0, int64_t v1) {
+            for (int64_t v = v0; v < v1; ++v) {
+                int32_t at = eptr[(size_t)v];
+                for (int64_t q = row_ptr[v]; q < row_ptr[v + 1]; ++q)
+                    if (above(v, src[q])) eidx[(size_t)at++] = src[q];
+            }
+        });
+    }
+    e = dev_alloc(&p, sizeof(int32_t) * (n + 1), c->stream);
+    if (e != cudaSuccess) return fail(cuda_status(e));
+    c->d_eptr = static_cast<int32_t *>(p);
+    e = dev_alloc(&p, sizeof(int32_t) * (size_t)(nnz / 2), c->stream);
+    if (e != cudaSuccess) return fail(cuda_status(e));
+    c->d_eidx = static_cast<int32_t *>(p);
+    if (cudaMemcpyAsync(c->d_eptr, eptr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(c->d_eidx, eidx.data(), sizeof(int32_t) * (size_t)(nnz / 2), cudaMemcpyHostToDevice,
+                        c->stream) != cudaSuccess)
+        return fail(MOCD_ERR_CUDA);
     int *d_bad = nullptr;
     int h_bad = 0;
     e = dev_alloc(reinterpret_cast<void **>(&d_bad), sizeof(int), c->stream);
@@ -1269,7 +1311,7 @@ static int batch_build(mocd_batch *b)
             mocd_ctx *c = b->ctx[(size_t)i];
             gps.push_back(c->gp);
             pss.push_back(c->ps);
-            mbs.push_back(BatchMember{c->gp, c->ps, c->d_row_ptr, c->d_col_idx, c->d_order});
+            mbs.push_back(BatchMember{c->gp, c->ps, c->d_row_ptr, c->d_col_idx, c->d_order, c->d_eptr, c->d_eidx});
             b->es_max = std::max(b->es_max, c->gp.es);
             // Per member and stage: its own grid (a deferred class's votes get
             // about one thread per four listed pairs at full capacity, at most
@@ -1583,6 +1625,8 @@ void mocd_destroy(mocd_ctx *c)
     dev_free(c->d_row_ptr, c->stream);
     dev_free(c->d_col_idx, c->stream);
     dev_free(c->d_order, c->stream);
+    dev_free(c->d_eptr, c->stream);
+    dev_free(c->d_eidx, c->stream);
     dev_free(c->d_im, c->stream);
     dev_free(c->d_nm, c->stream);
     dev_free(c->d_eval_acc, c->stream);

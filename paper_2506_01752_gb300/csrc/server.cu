@@ -320,7 +320,7 @@ int mocd_job_footprint(int64_t n, const int64_t *row_ptr, int32_t pop_size, int6
     const int64_t labels = 4 * n * W * 4;         // P halves, Q, post-crossover children
     const int64_t hist = W * n * 4;               // degree histogram
     const int64_t mutation = n * 4 + deferred_nodes * pop_size * 8 + hub_tables;  // hints, deferred votes
-    const int64_t graph = (n + 1) * 4 + nnz * 4 + n * 4 + 4;  // CSR, node order, symmetry flag
+    const int64_t graph = 2 * (n + 1) * 4 + (nnz + nnz / 2) * 4 + n * 4 + 4;  // CSR, oriented CSR, order, flag
     const int64_t front = (int64_t)pop_size * n * 4 + 2 * mocd::kMaxPop * 4;  // front download
     const int64_t fixed = (int64_t)1 << 20;       // small state, graph executable, events
     *bytes = labels + hist + mutation + graph + front + fixed;

@@ -33,12 +33,14 @@ def test_upload_allocation_failures():
     """Every allocation of mocd_graph_upload failing in turn: OUT_OF_MEMORY,
     no context; afterwards an upload succeeds."""
     rp, ci = _graph()
-    for k in range(4):  # CSR row pointers, adjacency, node order, symmetry flag
+    # CSR row pointers, adjacency, node order, the evaluation's oriented row
+    # pointers and adjacency, symmetry flag
+    for k in range(6):
         mocd.debug_inject(mocd.SITE_DEVICE_ALLOC, k, 1)
         with pytest.raises(mocd.MocdError) as e:
             mocd.graph_upload(rp, ci)
         assert e.value.status == OOM
-    mocd.debug_inject(mocd.SITE_DEVICE_ALLOC, 4, 1)  # a fifth allocation would fail: there is none
+    mocd.debug_inject(mocd.SITE_DEVICE_ALLOC, 6, 1)  # a seventh allocation would fail: there is none
     mocd.destroy(mocd.graph_upload(rp, ci))
 
 
