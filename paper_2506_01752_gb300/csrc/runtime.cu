@@ -941,42 +941,12 @@ int mocd_graph_upload(mocd_ctx **out, int64_t n, const int64_t *row_ptr, const i
     if (cudaMemcpyAsync(c->d_order, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->stream) !=
         cudaSuccess)
         return fail(MOCD_ERR_CUDA);
-    // The offspring evaluation's oriented adjacency: v lists u when (deg u, u)
-    // > (deg v, v), a strict total order, so every undirected edge is listed
-    // at exactly one endpoint.
-    std::vector<int32_t> eptr((size_t)n + 1, 0), eidx((size_t)(nnz / 2));
-    {
-        auto above = [&](int64_t v, int64_t u) {
-            const int64_t dv = row_ptr[v + 1] - row_ptr[v], du = row_ptr[u + 1] - row_ptr[u];
-            return du > dv || (du == dv && u > v);
-        };
-        parallel_rows(row_ptr, n, [&](int64_t v0, int64_t v1) {
-            for (int64_t v = v0; v < v1; ++v) {
-                int32_t k = 0;
-                for (int64_t q = row_ptr[v]; q < row_ptr[v + 1]; ++q) k += above(v, src[q]) ? 1 : 0;
-                eptr[(size_t)v + 1] = k;
-            }
-        });
-        for (int64_t v = 0; v < n; ++v) eptr[(size_t)v + 1] += eptr[(size_t)v];
-        parallel_rows(row_ptr, n, [&](int64_t v0, int64_t v1) {
-            for (int64_t v = v0; v < v1; ++v) {
-                int32_t at = eptr[(size_t)v];
-                for (int64_t q = row_ptr[v]; q < row_ptr[v + 1]; ++q)
-                    if (above(v, src[q])) eidx[(size_t)at++] = src[q];
-            }
-        });
-    }
     e = dev_alloc(&p, sizeof(int32_t) * (n + 1), c->stream);
     if (e != cudaSuccess) return fail(cuda_status(e));
     c->d_eptr = static_cast<int32_t *>(p);
     e = dev_alloc(&p, sizeof(int32_t) * (size_t)(nnz / 2), c->stream);
     if (e != cudaSuccess) return fail(cuda_status(e));
     c->d_eidx = static_cast<int32_t *>(p);
-    if (cudaMemcpyAsync(c->d_eptr, eptr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, c->stream) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(c->d_eidx, eidx.data(), sizeof(int32_t) * (size_t)(nnz / 2), cudaMemcpyHostToDevice,
-                        c->stream) != cudaSuccess)
-        return fail(MOCD_ERR_CUDA);
     int *d_bad = nullptr;
     int h_bad = 0;
     e = dev_alloc(reinterpret_cast<void **>(&d_bad), sizeof(int), c->stream);
@@ -988,6 +958,8 @@ int mocd_graph_upload(mocd_ctx **out, int64_t n, const int64_t *row_ptr, const i
             cudaSuccess &&
         cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream) == cudaSuccess &&
         launch_symmetry_check((int)n, c->d_row_ptr, c->d_col_idx, d_bad, c->sms, c->stream) == cudaSuccess &&
+        launch_orient((int)n, c->d_row_ptr, c->d_col_idx, c->d_eptr, c->d_eidx, (int)(nnz / 2), c->sms,
+                      c->stream) == cudaSuccess &&
         cudaMemcpyAsync(&h_bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream) == cudaSuccess;
     cudaFreeAsync(d_bad, c->stream);
     if (!copied || cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(MOCD_ERR_CUDA);
