@@ -88,6 +88,10 @@ typedef struct {
  * Rows may come in any order (a sorted copy is made when needed). The host
  * checks every row first (ids in range, self loops, repeats; the first
  * failing row decides the status), then symmetry is checked on the device.
+ * The context keeps on the device the CSR (4(n + 1) + 8m bytes), the nodes
+ * in degree order (4n) and, for the offspring evaluation, the adjacency with
+ * each undirected edge listed once (4(n + 1) + 4m); mocd_job_footprint
+ * counts them.
  * Errors: INVALID_ARG, NOT_SYMMETRIC, SELF_LOOP, DUPLICATE_EDGE, EMPTY_GRAPH,
  * OUT_OF_MEMORY, CUDA.
  */
