@@ -348,8 +348,10 @@ int prepare_population(mocd_ctx *c, const mocd_params *p)
     gp.hub_hs = hub_hs;
     gp.hub_warps = hub_warps;
     {
-        const int d0 = (int)std::min<int64_t>(std::max<int64_t>(c->dmax, 2 * 16 + 1), 2 * 32);  // degree class 33..64
-        gp.vote_n0 = (d0 + 7) / 8 * 8;
+        // The degree 33..64 vote's network holds the largest degree of that
+        // class in the graph: 40, 48, 56 or 64 entries.
+        const int64_t d0 = std::min<int64_t>(std::max<int64_t>(c->dmax, 33), 64);
+        gp.vote_n0 = (int)((d0 + 7) / 8 * 8);
     }
     gp.m = c->m;
     gp.key0 = (uint32_t)p->seed;
