@@ -159,13 +159,13 @@ cudaError_t launch_gather_individuals(int n, int W, int np, const int32_t *phalf
 // dst[v][k] = src[k][v] for k < count, zero for count <= k < W.
 cudaError_t launch_to_node_major(int n, int W, int count, const int32_t *src, int32_t *dst,
                                  cudaStream_t s);
-// *bad = 1 if some stored entry (v, u) has no mirror (u, v); rows must be
-// sorted, in range and free of self loops (checked on the host first).
 // The offspring evaluation's oriented adjacency of a host-checked CSR: eptr
 // [n + 1] row pointers, eidx [cap] entries (cap = m for a symmetric graph),
 // each undirected edge listed once, at its endpoint of lower (degree, id).
 cudaError_t launch_orient(int n, const int32_t *row_ptr, const int32_t *col_idx, int32_t *eptr, int32_t *eidx,
                           int cap, int sms, cudaStream_t s);
+// *bad = 1 if some stored entry (v, u) has no mirror (u, v); rows must be
+// sorted, in range and free of self loops (checked on the host first).
 cudaError_t launch_symmetry_check(int n, const int32_t *row_ptr, const int32_t *col_idx, int *bad, int sms,
                                   cudaStream_t s);
 // Debug-build bounds-check records of the kernel translation units
